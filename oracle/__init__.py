@@ -1,0 +1,207 @@
+"""FP64 CPU oracle for 3D Richardson-Lucy deconvolution -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+``paper_2510_14143_gb300``) never imports, links or executes it, and it never
+imports the product: the two share no code.  Inputs come from the seeded
+generator in ``paper_2510_14143_gb300.synth``, which holds none of the
+method's arithmetic.
+
+The arithmetic lives in ``rl_oracle.c`` (plain C, double precision, optional
+OpenMP); this module compiles it with gcc on first use and wraps it with
+ctypes.  It follows the paper's Section 4 "Richardson-Lucy deconvolution":
+forward convolution with the PSF, ratio with the observed image,
+back-convolution with the flipped PSF, multiplicative update.  The readings
+taken where the paper is silent (circular boundaries, PSF centre at
+floor(n/2), u0 = max(mean(d), eps), denominator clamp max(b, eps)) are stated
+in ``rl_oracle.c``.
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests
+in ``tests/test_oracle.py`` (brute-force DFT, direct convolution, closed-form
+RL cases, invariants, finite differences).  The paper prints no numerical RL
+example, so no pin comes from a value printed in the paper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rl_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile rl_oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER(ctypes.c_double)
+            i64, ci, cd = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            sig = {
+                "orc_num_threads": ([], ci),
+                "orc_fft1": ([P, i64, ci], ci),
+                "orc_dft1_brute": ([P, P, i64, ci], ci),
+                "orc_fft3": ([P, i64, i64, i64, ci], ci),
+                "orc_center_to_origin": ([P, P, i64, i64, i64], ci),
+                "orc_conv3_direct": ([P, P, P, i64, i64, i64], ci),
+                "orc_psf_spectrum": ([P, P, i64, i64, i64], ci),
+                "orc_convolve": ([P, P, P, i64, i64, i64, ci], ci),
+                "orc_initial_value": ([P, i64, cd], cd),
+                "orc_rl_iterate": ([P, P, P, cd, i64, i64, i64, P, P, P, P], ci),
+                "orc_rl": ([P, P, i64, i64, i64, ci, cd, P], ci),
+                "orc_rl_grad": ([P, P, i64, i64, i64, ci, cd, P, P, P], ci),
+                "orc_psf_gaussian": ([i64, i64, i64, cd, cd, cd, P], ci),
+                "orc_psf_gaussian_grad": ([i64, i64, i64, cd, cd, cd, P, P], ci),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with status {rc}")
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def fft1(x, inverse: bool = False) -> np.ndarray:
+    """Length-n DFT (radix-2, else Bluestein). Inverse carries 1/n."""
+    a = _c128(x).copy()
+    _check(_load().orc_fft1(_p(a.view(np.float64)), a.size, int(inverse)), "fft1")
+    return a
+
+
+def dft1_brute(x, inverse: bool = False) -> np.ndarray:
+    """O(n^2) DFT straight from its definition."""
+    a = _c128(x)
+    out = np.empty_like(a)
+    _check(_load().orc_dft1_brute(_p(a.view(np.float64)), _p(out.view(np.float64)), a.size,
+                                  int(inverse)), "dft1_brute")
+    return out
+
+
+def fft3(x, inverse: bool = False) -> np.ndarray:
+    """3D DFT of a [nz][ny][nx] array, axis by axis."""
+    a = _c128(x).copy()
+    nz, ny, nx = a.shape
+    _check(_load().orc_fft3(_p(a.view(np.float64)), nz, ny, nx, int(inverse)), "fft3")
+    return a
+
+
+def center_to_origin(p) -> np.ndarray:
+    a = _f64(p)
+    out = np.empty_like(a)
+    _check(_load().orc_center_to_origin(_p(a), _p(out), *a.shape), "center_to_origin")
+    return out
+
+
+def conv3_direct(h0, u) -> np.ndarray:
+    """Direct circular convolution out(y) = sum_x h0(x) u(y-x), O(V^2)."""
+    h, v = _f64(h0), _f64(u)
+    out = np.empty_like(v)
+    _check(_load().orc_conv3_direct(_p(h), _p(v), _p(out), *v.shape), "conv3_direct")
+    return out
+
+
+def psf_spectrum(psf) -> np.ndarray:
+    """H = DFT3 of the PSF moved from floor(n/2) to the origin."""
+    p = _f64(psf)
+    H = np.empty(p.shape, np.complex128)
+    _check(_load().orc_psf_spectrum(_p(p), _p(H.view(np.float64)), *p.shape), "psf_spectrum")
+    return H
+
+
+def convolve(H, u, flipped: bool = False) -> np.ndarray:
+    """Re IDFT3(H . DFT3(u)); with flipped=True uses conj(H) (the flipped PSF)."""
+    Hc, v = _c128(H), _f64(u)
+    out = np.empty_like(v)
+    _check(_load().orc_convolve(_p(Hc.view(np.float64)), _p(v), _p(out), *v.shape, int(flipped)),
+           "convolve")
+    return out
+
+
+def initial_value(d, eps: float) -> float:
+    a = _f64(d)
+    return float(_load().orc_initial_value(_p(a), a.size, float(eps)))
+
+
+def rl_iterate(H, d, u, eps: float):
+    """One RL iteration; returns (u_next, b, r, q)."""
+    Hc, dd, uu = _c128(H), _f64(d), _f64(u)
+    outs = [np.empty_like(uu) for _ in range(4)]
+    _check(_load().orc_rl_iterate(_p(Hc.view(np.float64)), _p(dd), _p(uu), float(eps), *uu.shape,
+                                  *[_p(o) for o in outs]), "rl_iterate")
+    return tuple(outs)
+
+
+def rl(d, psf, n_iter: int, eps: float = 1e-6) -> np.ndarray:
+    """n_iter RL iterations from u0 = max(mean(d), eps); float64 result."""
+    dd, p = _f64(d), _f64(psf)
+    if dd.shape != p.shape:
+        raise ValueError("image and PSF must have the same shape")
+    out = np.empty_like(dd)
+    _check(_load().orc_rl(_p(dd), _p(p), *dd.shape, int(n_iter), float(eps), _p(out)), "rl")
+    return out
+
+
+def rl_grad(d, psf, n_iter: int, eps: float, g_out):
+    """Reverse mode: returns (dL/dd, dL/dpsf) given dL/du_K = g_out."""
+    dd, p, g = _f64(d), _f64(psf), _f64(g_out)
+    gd, gp = np.empty_like(dd), np.empty_like(dd)
+    _check(_load().orc_rl_grad(_p(dd), _p(p), *dd.shape, int(n_iter), float(eps), _p(g), _p(gd),
+                               _p(gp)), "rl_grad")
+    return gd, gp
+
+
+def psf_gaussian(shape, sigma_xy: float, sigma_z: float, amp: float = 1.0) -> np.ndarray:
+    """A * g / sum(g), g an anisotropic Gaussian peaked at floor(n/2) per axis."""
+    out = np.empty(tuple(shape), np.float64)
+    _check(_load().orc_psf_gaussian(*out.shape, float(sigma_xy), float(sigma_z), float(amp), _p(out)),
+           "psf_gaussian")
+    return out
+
+
+def psf_gaussian_grad(shape, sigma_xy: float, sigma_z: float, amp: float, grad_psf) -> np.ndarray:
+    """(dL/dsigma_xy, dL/dsigma_z, dL/dA) from dL/dpsf."""
+    g = _f64(grad_psf)
+    out = np.empty(3, np.float64)
+    _check(_load().orc_psf_gaussian_grad(*tuple(shape), float(sigma_xy), float(sigma_z), float(amp),
+                                         _p(g), _p(out)), "psf_gaussian_grad")
+    return out

@@ -1,0 +1,510 @@
+/*
+ * rl_oracle.c -- FP64 CPU oracle for 3D Richardson-Lucy deconvolution.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library and
+ * its Python binding) links, loads or calls this file.  Only the tests, the
+ * smoke check and the CPU-baseline leg of the benchmark use it.  It shares no
+ * code, header, table or constant with the CUDA path.
+ *
+ * What it computes follows the paper (arXiv 2510.14143), Section 4,
+ * "Richardson-Lucy deconvolution": each iteration is (1) a forward
+ * convolution of the estimate with the PSF, (2) the ratio of the observed
+ * image to that blurred estimate, (3) a back-convolution of the ratio with the
+ * flipped PSF and (4) a multiplicative update of the estimate.  The same
+ * section states that the PSF has the same ZYX size as the image and that the
+ * convolutions are done with FFTs.  Where the paper is silent the oracle takes
+ * these readings (each listed in the design doc):
+ *   - circular boundaries (FFT convolution of same-size arrays, no padding);
+ *   - the PSF peak sits at index floor(n/2) on every axis and is moved to
+ *     the origin before the transform;
+ *   - "flipped PSF" is the circular flip h0(-x mod n), i.e. the adjoint of
+ *     the forward convolution (conj(H) in Fourier space);
+ *   - initial estimate u0 = max(mean(d), eps) everywhere;
+ *   - the ratio's denominator is clamped: r = d / max(b, eps).
+ *
+ * Everything is double precision, arrays are C-order [nz][ny][nx] (x fastest).
+ * FFT convention: forward X[k] = sum_n x[n] exp(-2 pi i k n / N), inverse
+ * carries 1/N per axis.  Transforms are full complex transforms; the real
+ * part is taken after each inverse (no half-spectrum tricks).
+ *
+ * FFT: iterative radix-2 decimation-in-time for powers of two; Bluestein's
+ * chirp-z method (built on the same radix-2 code) for every other length;
+ * an O(N^2) brute-force DFT for tests.
+ *
+ * Gradient: plain reverse mode over the same steps, storing every iterate.
+ * Gaussian PSF: h = A * g / sum(g), g = exp(-(dx^2+dy^2)/(2 sxy^2) - dz^2/(2 sz^2)),
+ * (dx,dy,dz) = index - floor(n/2).
+ *
+ * All entry points return 0 on success and a negative value on bad input or
+ * allocation failure.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+static const double PI = 3.14159265358979323846264338327950288;
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+/* ---------------------------------------------------------------- FFT 1D */
+
+/* In-place iterative radix-2 DIT FFT, forward (sign=-1) or unnormalised
+ * backward (sign=+1).  n must be a power of two. */
+static void fft_radix2(cplx *x, int64_t n, int sign)
+{
+    /* bit-reversal permutation */
+    for (int64_t i = 1, j = 0; i < n; ++i) {
+        int64_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) { cplx t = x[i]; x[i] = x[j]; x[j] = t; }
+    }
+    for (int64_t len = 2; len <= n; len <<= 1) {
+        int64_t half = len / 2;
+        for (int64_t k = 0; k < half; ++k) {
+            double a = sign * 2.0 * PI * (double)k / (double)len;
+            cplx w = cos(a) + I * sin(a);
+            for (int64_t s = 0; s < n; s += len) {
+                cplx e = x[s + k];
+                cplx o = x[s + k + half] * w;
+                x[s + k] = e + o;
+                x[s + k + half] = e - o;
+            }
+        }
+    }
+}
+
+/* Bluestein / chirp-z: length-n DFT as a circular convolution of length
+ * m >= 2n-1 (m a power of two) done with radix-2 FFTs.
+ * exp(sign*2 pi i k j/n) = w_k w_j conj(w_{k-j}) with w_j = exp(sign*pi i j^2/n). */
+static int fft_bluestein(cplx *x, int64_t n, int sign)
+{
+    int64_t m = 1;
+    while (m < 2 * n - 1) m <<= 1;
+    cplx *w = malloc(sizeof(cplx) * (size_t)n);
+    cplx *a = calloc((size_t)m, sizeof(cplx));
+    cplx *b = calloc((size_t)m, sizeof(cplx));
+    if (!w || !a || !b) { free(w); free(a); free(b); return -2; }
+    for (int64_t j = 0; j < n; ++j) {
+        /* reduce j^2 modulo 2n so the angle stays small and exact */
+        int64_t jj = (int64_t)(((__int128)j * j) % (2 * n));
+        double ang = sign * PI * (double)jj / (double)n;
+        w[j] = cos(ang) + I * sin(ang);
+    }
+    for (int64_t j = 0; j < n; ++j) a[j] = x[j] * w[j];
+    b[0] = conj(w[0]);
+    for (int64_t j = 1; j < n; ++j) { b[j] = conj(w[j]); b[m - j] = conj(w[j]); }
+    fft_radix2(a, m, -1);
+    fft_radix2(b, m, -1);
+    for (int64_t j = 0; j < m; ++j) a[j] *= b[j];
+    fft_radix2(a, m, +1);
+    for (int64_t k = 0; k < n; ++k) x[k] = w[k] * a[k] / (double)m;
+    free(w); free(a); free(b);
+    return 0;
+}
+
+/* Forward (inverse=0) or inverse (inverse=1, with 1/n) DFT of one line. */
+static int fft_line(cplx *x, int64_t n, int inverse)
+{
+    int sign = inverse ? +1 : -1;
+    int rc = 0;
+    if (n == 1) return 0;
+    if (is_pow2(n)) fft_radix2(x, n, sign);
+    else rc = fft_bluestein(x, n, sign);
+    if (inverse) for (int64_t k = 0; k < n; ++k) x[k] /= (double)n;
+    return rc;
+}
+
+/* x: interleaved (re, im) doubles, length n; transformed in place. */
+int orc_fft1(double *x, int64_t n, int inverse)
+{
+    if (!x || n < 1) return -1;
+    return fft_line((cplx *)x, n, inverse);
+}
+
+/* Brute-force O(n^2) DFT, out of place. */
+int orc_dft1_brute(const double *in, double *out, int64_t n, int inverse)
+{
+    if (!in || !out || n < 1) return -1;
+    const cplx *xi = (const cplx *)in;
+    cplx *xo = (cplx *)out;
+    int sign = inverse ? +1 : -1;
+    for (int64_t k = 0; k < n; ++k) {
+        cplx s = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            int64_t kj = (int64_t)(((__int128)k * j) % n);
+            double a = sign * 2.0 * PI * (double)kj / (double)n;
+            s += xi[j] * (cos(a) + I * sin(a));
+        }
+        xo[k] = inverse ? s / (double)n : s;
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- FFT 3D */
+
+/* Transform every line along one axis of a [nz][ny][nx] complex array.
+ * stride = distance between consecutive elements of a line, count = lines. */
+static int fft_axis(cplx *x, int64_t nz, int64_t ny, int64_t nx, int axis, int inverse)
+{
+    int64_t n, stride;
+    if (axis == 2) { n = nx; stride = 1; }
+    else if (axis == 1) { n = ny; stride = nx; }
+    else { n = nz; stride = nx * ny; }
+    if (n == 1) return 0;
+    int64_t lines = nx * ny * nz / n;
+    int err = 0;
+#pragma omp parallel
+    {
+        cplx *buf = malloc(sizeof(cplx) * (size_t)n);
+        if (!buf) {
+#pragma omp atomic write
+            err = -2;
+        } else {
+#pragma omp for schedule(static)
+            for (int64_t l = 0; l < lines; ++l) {
+                /* first element of line l */
+                int64_t base;
+                if (axis == 2) base = l * nx;
+                else if (axis == 1) base = (l / nx) * nx * ny + (l % nx);
+                else base = l;
+                for (int64_t j = 0; j < n; ++j) buf[j] = x[base + j * stride];
+                if (fft_line(buf, n, inverse) != 0) {
+#pragma omp atomic write
+                    err = -2;
+                }
+                for (int64_t j = 0; j < n; ++j) x[base + j * stride] = buf[j];
+            }
+            free(buf);
+        }
+    }
+    return err;
+}
+
+static int fft3(cplx *x, int64_t nz, int64_t ny, int64_t nx, int inverse)
+{
+    int rc = 0;
+    for (int axis = 2; axis >= 0 && rc == 0; --axis)
+        rc = fft_axis(x, nz, ny, nx, axis, inverse);
+    return rc;
+}
+
+int orc_fft3(double *x, int64_t nz, int64_t ny, int64_t nx, int inverse)
+{
+    if (!x || nz < 1 || ny < 1 || nx < 1) return -1;
+    return fft3((cplx *)x, nz, ny, nx, inverse);
+}
+
+/* ------------------------------------------------------- PSF and helpers */
+
+static int64_t wrap(int64_t i, int64_t n) { int64_t r = i % n; return r < 0 ? r + n : r; }
+
+/* h0(z,y,x) = p((z + nz/2) mod nz, (y + ny/2) mod ny, (x + nx/2) mod nx):
+ * moves the PSF peak from floor(n/2) to the origin. */
+static void center_to_origin(const double *p, double *h0, int64_t nz, int64_t ny, int64_t nx)
+{
+    int64_t cz = nz / 2, cy = ny / 2, cx = nx / 2;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x)
+                h0[(z * ny + y) * nx + x] =
+                    p[(wrap(z + cz, nz) * ny + wrap(y + cy, ny)) * nx + wrap(x + cx, nx)];
+}
+
+/* inverse map: p(x) = h0(x - c) */
+static void origin_to_center(const double *h0, double *p, int64_t nz, int64_t ny, int64_t nx)
+{
+    int64_t cz = nz / 2, cy = ny / 2, cx = nx / 2;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x)
+                p[(wrap(z + cz, nz) * ny + wrap(y + cy, ny)) * nx + wrap(x + cx, nx)] =
+                    h0[(z * ny + y) * nx + x];
+}
+
+int orc_center_to_origin(const double *p, double *h0, int64_t nz, int64_t ny, int64_t nx)
+{
+    if (!p || !h0 || nz < 1 || ny < 1 || nx < 1) return -1;
+    center_to_origin(p, h0, nz, ny, nx);
+    return 0;
+}
+
+/* Direct circular convolution, O(V^2): out(y) = sum_x h0(x) u(y - x). */
+int orc_conv3_direct(const double *h0, const double *u, double *out,
+                     int64_t nz, int64_t ny, int64_t nx)
+{
+    if (!h0 || !u || !out || nz < 1 || ny < 1 || nx < 1) return -1;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                double s = 0.0;
+                for (int64_t a = 0; a < nz; ++a)
+                    for (int64_t b = 0; b < ny; ++b)
+                        for (int64_t c = 0; c < nx; ++c)
+                            s += h0[(a * ny + b) * nx + c] *
+                                 u[(wrap(z - a, nz) * ny + wrap(y - b, ny)) * nx + wrap(x - c, nx)];
+                out[(z * ny + y) * nx + x] = s;
+            }
+    return 0;
+}
+
+/* ------------------------------------------------------------ RL oracle */
+
+/* Spectrum of the origin-centred PSF: H = DFT3(h0). Hs: interleaved complex, V. */
+int orc_psf_spectrum(const double *psf, double *Hs, int64_t nz, int64_t ny, int64_t nx)
+{
+    if (!psf || !Hs || nz < 1 || ny < 1 || nx < 1) return -1;
+    int64_t V = nz * ny * nx;
+    double *h0 = malloc(sizeof(double) * (size_t)V);
+    if (!h0) return -2;
+    center_to_origin(psf, h0, nz, ny, nx);
+    cplx *H = (cplx *)Hs;
+    for (int64_t i = 0; i < V; ++i) H[i] = h0[i];
+    free(h0);
+    return fft3(H, nz, ny, nx, 0);
+}
+
+/* out = Re IDFT3(M(H) * DFT3(in)), M = identity (conjugate=0) or conj (=1).
+ * work: V complex scratch. */
+static int spectral_filter(const cplx *H, const double *in, double *out, cplx *work,
+                           int64_t nz, int64_t ny, int64_t nx, int conjugate)
+{
+    int64_t V = nz * ny * nx;
+    for (int64_t i = 0; i < V; ++i) work[i] = in[i];
+    int rc = fft3(work, nz, ny, nx, 0);
+    if (rc) return rc;
+    for (int64_t i = 0; i < V; ++i) work[i] *= conjugate ? conj(H[i]) : H[i];
+    rc = fft3(work, nz, ny, nx, 1);
+    if (rc) return rc;
+    for (int64_t i = 0; i < V; ++i) out[i] = creal(work[i]);
+    return 0;
+}
+
+/* Blur with the PSF (b = h * u, circular) -- the forward model, given H. */
+int orc_convolve(const double *Hs, const double *u, double *b, int64_t nz, int64_t ny, int64_t nx,
+                 int conjugate)
+{
+    if (!Hs || !u || !b || nz < 1 || ny < 1 || nx < 1) return -1;
+    int64_t V = nz * ny * nx;
+    cplx *work = malloc(sizeof(cplx) * (size_t)V);
+    if (!work) return -2;
+    int rc = spectral_filter((const cplx *)Hs, u, b, work, nz, ny, nx, conjugate);
+    free(work);
+    return rc;
+}
+
+double orc_initial_value(const double *d, int64_t V, double eps)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < V; ++i) s += d[i];
+    double m = s / (double)V;
+    return m > eps ? m : eps;
+}
+
+/* One RL iteration from u (given H).  Writes u_next and, if non-NULL, the
+ * intermediates b = h*u, r = d/max(b,eps), q = h (flipped) * r. */
+int orc_rl_iterate(const double *Hs, const double *d, const double *u, double eps,
+                   int64_t nz, int64_t ny, int64_t nx,
+                   double *u_next, double *b_out, double *r_out, double *q_out)
+{
+    if (!Hs || !d || !u || !u_next || nz < 1 || ny < 1 || nx < 1) return -1;
+    int64_t V = nz * ny * nx;
+    cplx *work = malloc(sizeof(cplx) * (size_t)V);
+    double *b = malloc(sizeof(double) * (size_t)V);
+    double *r = malloc(sizeof(double) * (size_t)V);
+    double *q = malloc(sizeof(double) * (size_t)V);
+    int rc = -2;
+    if (work && b && r && q) {
+        const cplx *H = (const cplx *)Hs;
+        rc = spectral_filter(H, u, b, work, nz, ny, nx, 0);           /* forward conv */
+        if (!rc) {
+            for (int64_t i = 0; i < V; ++i) {                           /* ratio */
+                double c = b[i] > eps ? b[i] : eps;
+                r[i] = d[i] / c;
+            }
+            rc = spectral_filter(H, r, q, work, nz, ny, nx, 1);        /* back-conv, flipped PSF */
+        }
+        if (!rc) {
+            for (int64_t i = 0; i < V; ++i) u_next[i] = u[i] * q[i];   /* multiplicative update */
+            if (b_out) memcpy(b_out, b, sizeof(double) * (size_t)V);
+            if (r_out) memcpy(r_out, r, sizeof(double) * (size_t)V);
+            if (q_out) memcpy(q_out, q, sizeof(double) * (size_t)V);
+        }
+    }
+    free(work); free(b); free(r); free(q);
+    return rc;
+}
+
+/* Full RL: n_iter iterations from u0 = max(mean(d), eps). */
+int orc_rl(const double *d, const double *psf, int64_t nz, int64_t ny, int64_t nx,
+           int n_iter, double eps, double *out)
+{
+    if (!d || !psf || !out || nz < 1 || ny < 1 || nx < 1 || n_iter < 0 || !(eps > 0)) return -1;
+    int64_t V = nz * ny * nx;
+    double *Hs = malloc(sizeof(double) * 2 * (size_t)V);
+    double *u = malloc(sizeof(double) * (size_t)V);
+    if (!Hs || !u) { free(Hs); free(u); return -2; }
+    int rc = orc_psf_spectrum(psf, Hs, nz, ny, nx);
+    double u0 = orc_initial_value(d, V, eps);
+    for (int64_t i = 0; i < V; ++i) u[i] = u0;
+    for (int k = 0; k < n_iter && !rc; ++k)
+        rc = orc_rl_iterate(Hs, d, u, eps, nz, ny, nx, u, NULL, NULL, NULL);
+    if (!rc) memcpy(out, u, sizeof(double) * (size_t)V);
+    free(Hs); free(u);
+    return rc;
+}
+
+/* Reverse mode through n_iter RL iterations.
+ * g_out = dL/du_K.  Writes grad_d = dL/dd (through the ratio at every
+ * iteration and through u0 = max(mean(d), eps)) and grad_psf = dL/dp for the
+ * centred PSF p.  Either output may be NULL. */
+int orc_rl_grad(const double *d, const double *psf, int64_t nz, int64_t ny, int64_t nx,
+                int n_iter, double eps, const double *g_out, double *grad_d, double *grad_psf)
+{
+    if (!d || !psf || !g_out || nz < 1 || ny < 1 || nx < 1 || n_iter < 0 || !(eps > 0)) return -1;
+    int64_t V = nz * ny * nx;
+    size_t fb = sizeof(double) * (size_t)V;
+    int K = n_iter;
+    double *Hs = malloc(2 * fb);
+    double *us = malloc(fb * (size_t)(K + 1));   /* u_0 .. u_K */
+    double *bs = malloc(fb * (size_t)(K > 0 ? K : 1));
+    double *qs = malloc(fb * (size_t)(K > 0 ? K : 1));
+    double *rs = malloc(fb * (size_t)(K > 0 ? K : 1));
+    double *gu = malloc(fb), *qb = malloc(fb), *rb = malloc(fb), *bb = malloc(fb), *tmp = malloc(fb);
+    double *gd = calloc((size_t)V, sizeof(double));
+    cplx *G = calloc((size_t)V, sizeof(cplx));     /* spectrum of dL/dh0 */
+    cplx *w1 = malloc(sizeof(cplx) * (size_t)V), *w2 = malloc(sizeof(cplx) * (size_t)V);
+    int rc = -2;
+    if (!Hs || !us || !bs || !qs || !rs || !gu || !qb || !rb || !bb || !tmp || !gd || !G || !w1 || !w2)
+        goto done;
+    rc = orc_psf_spectrum(psf, Hs, nz, ny, nx);
+    if (rc) goto done;
+    const cplx *H = (const cplx *)Hs;
+    double u0 = orc_initial_value(d, V, eps);
+    for (int64_t i = 0; i < V; ++i) us[i] = u0;
+    for (int k = 0; k < K && !rc; ++k)
+        rc = orc_rl_iterate(Hs, d, us + (size_t)k * V, eps, nz, ny, nx,
+                            us + (size_t)(k + 1) * V, bs + (size_t)k * V, rs + (size_t)k * V,
+                            qs + (size_t)k * V);
+    if (rc) goto done;
+
+    memcpy(gu, g_out, fb);
+    for (int k = K - 1; k >= 0 && !rc; --k) {
+        const double *u = us + (size_t)k * V, *b = bs + (size_t)k * V;
+        const double *r = rs + (size_t)k * V, *q = qs + (size_t)k * V;
+        /* u_{k+1} = u * q */
+        for (int64_t i = 0; i < V; ++i) { qb[i] = gu[i] * u[i]; gu[i] = gu[i] * q[i]; }
+        /* q = corr(h, r): adjoint is convolution with h */
+        rc = spectral_filter(H, qb, rb, w1, nz, ny, nx, 0);
+        if (rc) break;
+        /* r = d / c, c = max(b, eps) */
+        for (int64_t i = 0; i < V; ++i) {
+            double c = b[i] > eps ? b[i] : eps;
+            gd[i] += rb[i] / c;
+            double cb = -rb[i] * d[i] / (c * c);
+            bb[i] = b[i] > eps ? cb : 0.0;
+        }
+        /* b = conv(h, u): adjoint is correlation with h */
+        rc = spectral_filter(H, bb, tmp, w1, nz, ny, nx, 1);
+        if (rc) break;
+        for (int64_t i = 0; i < V; ++i) gu[i] += tmp[i];
+        /* PSF: dL/dh0 += corr(bbar, u) + corr(r, qbar)
+         *   F[sum_y bb(y) u(y-x)] = BB conj(U);  F[sum_y qb(y) r(y+x)] = conj(QB) R */
+        for (int64_t i = 0; i < V; ++i) { w1[i] = bb[i]; w2[i] = u[i]; }
+        if ((rc = fft3(w1, nz, ny, nx, 0)) || (rc = fft3(w2, nz, ny, nx, 0))) break;
+        for (int64_t i = 0; i < V; ++i) G[i] += w1[i] * conj(w2[i]);
+        for (int64_t i = 0; i < V; ++i) { w1[i] = qb[i]; w2[i] = r[i]; }
+        if ((rc = fft3(w1, nz, ny, nx, 0)) || (rc = fft3(w2, nz, ny, nx, 0))) break;
+        for (int64_t i = 0; i < V; ++i) G[i] += conj(w1[i]) * w2[i];
+    }
+    if (rc) goto done;
+    /* u0 = max(mean(d), eps) */
+    {
+        double s = 0.0, sd = 0.0;
+        for (int64_t i = 0; i < V; ++i) { s += gu[i]; sd += d[i]; }
+        if (sd / (double)V > eps)
+            for (int64_t i = 0; i < V; ++i) gd[i] += s / (double)V;
+    }
+    if (grad_d) memcpy(grad_d, gd, fb);
+    if (grad_psf) {
+        rc = fft3(G, nz, ny, nx, 1);
+        if (rc) goto done;
+        for (int64_t i = 0; i < V; ++i) tmp[i] = creal(G[i]);
+        origin_to_center(tmp, grad_psf, nz, ny, nx);
+    }
+done:
+    free(Hs); free(us); free(bs); free(qs); free(rs);
+    free(gu); free(qb); free(rb); free(bb); free(tmp); free(gd); free(G); free(w1); free(w2);
+    return rc;
+}
+
+/* ------------------------------------------------------- Gaussian PSF */
+
+static double gauss_g(int64_t z, int64_t y, int64_t x, int64_t nz, int64_t ny, int64_t nx,
+                      double sxy, double sz, double *rxy2, double *rz2)
+{
+    double dz = (double)(z - nz / 2), dy = (double)(y - ny / 2), dx = (double)(x - nx / 2);
+    double a = dx * dx + dy * dy, c = dz * dz;
+    if (rxy2) *rxy2 = a;
+    if (rz2) *rz2 = c;
+    return exp(-a / (2.0 * sxy * sxy) - c / (2.0 * sz * sz));
+}
+
+/* psf = A * g / sum(g) */
+int orc_psf_gaussian(int64_t nz, int64_t ny, int64_t nx, double sxy, double sz, double amp, double *psf)
+{
+    if (!psf || nz < 1 || ny < 1 || nx < 1 || !(sxy > 0) || !(sz > 0)) return -1;
+    double s = 0.0;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                double g = gauss_g(z, y, x, nz, ny, nx, sxy, sz, NULL, NULL);
+                psf[(z * ny + y) * nx + x] = g;
+                s += g;
+            }
+    for (int64_t i = 0; i < nz * ny * nx; ++i) psf[i] *= amp / s;
+    return 0;
+}
+
+/* Chain rule through psf = A g / S, S = sum g:
+ *   dL/dA   = sum(gp * g) / S
+ *   dL/dsig = A/S * [sum(gp * dg) - sum(gp * g) * sum(dg) / S],
+ *   dg/dsxy = g (dx^2+dy^2) / sxy^3,  dg/dsz = g dz^2 / sz^3.
+ * out3 = {dL/dsxy, dL/dsz, dL/dA}. */
+int orc_psf_gaussian_grad(int64_t nz, int64_t ny, int64_t nx, double sxy, double sz, double amp,
+                          const double *grad_psf, double *out3)
+{
+    if (!grad_psf || !out3 || nz < 1 || ny < 1 || nx < 1 || !(sxy > 0) || !(sz > 0)) return -1;
+    double S = 0, Sxy = 0, Sz = 0, Pg = 0, Pxy = 0, Pz = 0;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                double a, c;
+                double g = gauss_g(z, y, x, nz, ny, nx, sxy, sz, &a, &c);
+                double gxy = g * a / (sxy * sxy * sxy);
+                double gz = g * c / (sz * sz * sz);
+                double p = grad_psf[(z * ny + y) * nx + x];
+                S += g; Sxy += gxy; Sz += gz;
+                Pg += p * g; Pxy += p * gxy; Pz += p * gz;
+            }
+    out3[0] = amp / S * (Pxy - Pg * Sxy / S);
+    out3[1] = amp / S * (Pz - Pg * Sz / S);
+    out3[2] = Pg / S;
+    return 0;
+}

@@ -1,0 +1,416 @@
+"""Pins for the FP64 oracle, checked against things other than itself.
+
+Each check follows from the definition of the DFT, of circular convolution or
+from properties of Richardson-Lucy (RL) iteration that the paper's Section 4
+"Richardson-Lucy deconvolution" implies (Poisson maximum likelihood, forward
+convolution / ratio / flipped-PSF back-convolution / multiplicative update).
+Every check is chosen so that a plausible slip in the oracle (a dropped term,
+a wrong sign or conjugation, an off-by-one PSF centre, a swapped ratio) fails
+at least one of them.  No test here needs a GPU.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_14143_gb300 import synth
+
+RNG = np.random.default_rng(12345)
+
+
+def crand(n, seed):
+    r = np.random.default_rng(seed)
+    return r.standard_normal(n) + 1j * r.standard_normal(n)
+
+
+def dft_matrix(n, sign=-1):
+    k = np.arange(n)
+    return np.exp(sign * 2j * np.pi * np.outer(k, k) / n)
+
+
+# ---------------------------------------------------------------- 1D FFT
+
+LENGTHS = [1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 15, 16, 25, 27, 30, 32, 48, 50, 64, 75, 81, 96, 125, 128,
+           135, 160]
+
+
+@pytest.mark.parametrize("n", LENGTHS)
+def test_fft1_matches_brute_dft(n):
+    x = crand(n, n)
+    ref = dft_matrix(n) @ x                          # definition, written here
+    assert np.allclose(oracle.fft1(x), ref, rtol=0, atol=1e-11 * max(1, np.abs(ref).max()))
+    assert np.allclose(oracle.dft1_brute(x), ref, rtol=0, atol=1e-11 * max(1, np.abs(ref).max()))
+    inv = (dft_matrix(n, +1) @ x) / n
+    assert np.allclose(oracle.fft1(x, inverse=True), inv, rtol=0, atol=1e-12 * max(1, np.abs(inv).max()))
+
+
+@pytest.mark.parametrize("n", [8, 12, 75, 128])
+def test_fft1_closed_forms(n):
+    # delta at m  ->  exp(-2 pi i k m / n)
+    m = 3 % n
+    x = np.zeros(n, complex)
+    x[m] = 1
+    k = np.arange(n)
+    assert np.allclose(oracle.fft1(x), np.exp(-2j * np.pi * k * m / n), atol=1e-13)
+    # pure tone exp(+2 pi i m j / n) -> n * delta(k - m): fixes the sign convention
+    tone = np.exp(2j * np.pi * m * k / n)
+    out = oracle.fft1(tone)
+    expect = np.zeros(n, complex)
+    expect[m] = n
+    assert np.allclose(out, expect, atol=1e-10)
+    # constant -> n at DC
+    c = oracle.fft1(np.full(n, 2.5 + 0j))
+    assert abs(c[0] - 2.5 * n) < 1e-10 and np.abs(c[1:]).max() < 1e-10
+
+
+@pytest.mark.parametrize("n", [48, 75, 81, 1024, 160])
+def test_fft1_roundtrip_and_parseval(n):
+    x = crand(n, 7 * n)
+    X = oracle.fft1(x)
+    assert np.allclose(oracle.fft1(X, inverse=True), x, atol=1e-12)
+    assert np.isclose((np.abs(X) ** 2).sum(), n * (np.abs(x) ** 2).sum(), rtol=1e-12)
+
+
+def test_fft1_library_cross_check():
+    # a special case that reduces to a library routine
+    for n in (54, 100, 144, 150, 2160, 2560):
+        x = crand(n, n + 1)
+        assert np.allclose(oracle.fft1(x), np.fft.fft(x), atol=1e-9 * np.sqrt(n))
+
+
+# ---------------------------------------------------------------- 3D FFT
+
+@pytest.mark.parametrize("shape", [(4, 6, 5), (3, 5, 7), (8, 8, 8), (1, 1, 6), (2, 1, 3)])
+def test_fft3_matches_brute(shape):
+    x = crand(int(np.prod(shape)), 99).reshape(shape)
+    Fz, Fy, Fx = (dft_matrix(n) for n in shape)
+    ref = np.einsum("ai,bj,ck,ijk->abc", Fz, Fy, Fx, x)
+    assert np.allclose(oracle.fft3(x), ref, atol=1e-10)
+    assert np.allclose(oracle.fft3(ref, inverse=True), x, atol=1e-12)
+    # Hermitian symmetry of the transform of a real field
+    X = oracle.fft3(x.real)
+    idx = tuple(np.ix_(*[(-np.arange(n)) % n for n in shape]))
+    assert np.allclose(X, np.conj(X[idx]), atol=1e-10)
+
+
+# ----------------------------------------------------------- convolution
+
+def direct_circular_conv(h0, u):
+    """out(y) = sum_x h0(x) u(y - x), written out with Python loops."""
+    nz, ny, nx = u.shape
+    out = np.zeros_like(u, dtype=np.float64)
+    for (z, y, x) in itertools.product(range(nz), range(ny), range(nx)):
+        s = 0.0
+        for (a, b, c) in itertools.product(range(nz), range(ny), range(nx)):
+            s += h0[a, b, c] * u[(z - a) % nz, (y - b) % ny, (x - c) % nx]
+        out[z, y, x] = s
+    return out
+
+
+def test_center_to_origin_definition():
+    shape = (3, 4, 5)
+    p = np.arange(60, dtype=float).reshape(shape)
+    h0 = oracle.center_to_origin(p)
+    # the PSF centre floor(n/2) lands on the origin
+    assert h0[0, 0, 0] == p[1, 2, 2]
+    assert h0[0, 0, 1] == p[1, 2, 3]
+    assert h0[0, 0, 4] == p[1, 2, 1]          # x = -1 wraps
+    assert h0[2, 3, 0] == p[0, 1, 2]          # z = -1, y = -1
+
+
+def test_convolution_against_direct_loops():
+    shape = (3, 4, 5)
+    r = np.random.default_rng(5)
+    psf = r.uniform(0.1, 1.0, shape)          # deliberately not symmetric
+    u = r.uniform(0.5, 2.0, shape)
+    h0 = oracle.center_to_origin(psf)
+    ref = direct_circular_conv(h0, u)
+    H = oracle.psf_spectrum(psf)
+    assert np.allclose(oracle.convolve(H, u), ref, atol=1e-12)
+    assert np.allclose(oracle.conv3_direct(h0, u), ref, atol=1e-12)
+    # the flipped PSF is the circular flip h0(-x)
+    flip = h0[tuple(np.ix_(*[(-np.arange(n)) % n for n in shape]))]
+    assert np.allclose(oracle.convolve(H, u, flipped=True), direct_circular_conv(flip, u), atol=1e-12)
+
+
+def test_delta_psf_centering():
+    shape = (4, 6, 5)
+    u = np.random.default_rng(2).uniform(size=shape)
+    c = tuple(n // 2 for n in shape)
+    delta = np.zeros(shape)
+    delta[c] = 1.0
+    assert np.allclose(oracle.convolve(oracle.psf_spectrum(delta), u), u, atol=1e-13)
+    # a delta one voxel right of the centre shifts the image by +1 along x
+    delta2 = np.zeros(shape)
+    delta2[c[0], c[1], c[2] + 1] = 1.0
+    assert np.allclose(oracle.convolve(oracle.psf_spectrum(delta2), u), np.roll(u, 1, axis=2), atol=1e-13)
+    # ... and one voxel up in z shifts by +1 along z
+    delta3 = np.zeros(shape)
+    delta3[c[0] + 1, c[1], c[2]] = 1.0
+    assert np.allclose(oracle.convolve(oracle.psf_spectrum(delta3), u), np.roll(u, 1, axis=0), atol=1e-13)
+
+
+def test_adjoint_identity():
+    shape = (6, 5, 4)
+    r = np.random.default_rng(11)
+    psf = r.uniform(size=shape)
+    H = oracle.psf_spectrum(psf)
+    x, y = r.standard_normal(shape), r.standard_normal(shape)
+    lhs = np.vdot(oracle.convolve(H, x), y)
+    rhs = np.vdot(x, oracle.convolve(H, y, flipped=True))
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs) * 10
+
+
+# --------------------------------------------------------------- RL
+
+def brute_rl(d, psf, n_iter, eps):
+    """Second RL path: direct spatial convolutions, no FFT."""
+    shape = d.shape
+    h0 = oracle.center_to_origin(psf)
+    flip = h0[tuple(np.ix_(*[(-np.arange(n)) % n for n in shape]))]
+    u = np.full(shape, max(d.mean(), eps))
+    for _ in range(n_iter):
+        b = direct_circular_conv(h0, u)
+        r = d / np.maximum(b, eps)
+        q = direct_circular_conv(flip, r)
+        u = u * q
+    return u
+
+
+def test_rl_matches_spatial_path():
+    shape = (3, 4, 5)
+    r = np.random.default_rng(21)
+    d = r.uniform(1.0, 10.0, shape)
+    psf = r.uniform(0.05, 1.0, shape)
+    psf /= psf.sum()
+    assert np.allclose(oracle.rl(d, psf, 4, 1e-6), brute_rl(d, psf, 4, 1e-6), rtol=1e-12, atol=0)
+
+
+def test_rl_zero_iterations_is_initial_estimate():
+    d = np.random.default_rng(3).uniform(0, 5, (4, 4, 4))
+    out = oracle.rl(d, np.ones((4, 4, 4)) / 64, 0, 1e-6)
+    assert np.allclose(out, d.mean())
+    assert np.allclose(oracle.rl(np.zeros((2, 2, 2)), np.ones((2, 2, 2)), 0, 1e-3), 1e-3)
+
+
+def test_rl_delta_psf_fixed_point():
+    shape = (4, 6, 5)
+    d = np.random.default_rng(4).uniform(1, 100, shape)
+    psf = np.zeros(shape)
+    psf[tuple(n // 2 for n in shape)] = 1.0
+    for k in (1, 2, 5):
+        assert np.allclose(oracle.rl(d, psf, k, 1e-6), d, rtol=1e-12)
+
+
+def test_rl_constant_image():
+    shape = (4, 5, 6)
+    psf = np.random.default_rng(8).uniform(size=shape)
+    psf /= psf.sum()
+    d = np.full(shape, 7.25)
+    assert np.allclose(oracle.rl(d, psf, 5, 1e-6), 7.25, rtol=1e-12)
+
+
+def test_rl_single_voxel():
+    assert np.allclose(oracle.rl(np.array([[[3.5]]]), np.array([[[0.3]]]), 1, 1e-6), 3.5)
+
+
+def test_rl_first_iterate_closed_form():
+    # from a constant start: u1 = (h flipped * d) / sum(h), independent of u0
+    shape = (4, 5, 6)
+    r = np.random.default_rng(9)
+    psf = r.uniform(size=shape)
+    d = r.uniform(1, 50, shape)
+    h0 = oracle.center_to_origin(psf)
+    flip = h0[tuple(np.ix_(*[(-np.arange(n)) % n for n in shape]))]
+    expect = direct_circular_conv(flip, d) / psf.sum()
+    assert np.allclose(oracle.rl(d, psf, 1, 1e-6), expect, rtol=1e-12)
+
+
+def test_rl_scale_invariance_flux_nonnegativity():
+    d, _ = synth.workload_volume(synth.SMALL)
+    psf = oracle.psf_gaussian(d.shape, 1.5, 3.0)
+    u = oracle.rl(d, psf, 6, 1e-6)
+    u_scaled = oracle.rl(d, 3.0 * psf, 6, 1e-6)
+    assert np.allclose(u, u_scaled, rtol=1e-10, atol=1e-9)
+    # total flux is conserved for k >= 1 (clamp inactive)
+    assert abs(u.sum() - d.astype(np.float64).sum()) <= 1e-10 * d.sum()
+    assert u.min() >= 0.0
+
+
+def test_rl_poisson_likelihood_monotone():
+    shape = (8, 12, 10)
+    d, _ = synth.make_volume(shape, 4, (1.5, 2.5), 5.0, 1.2, 2.0, 777)
+    d = d.astype(np.float64)
+    psf = oracle.psf_gaussian(shape, 1.2, 2.0)
+    H = oracle.psf_spectrum(psf)
+    u = np.full(shape, d.mean())
+    prev = np.inf
+    for _ in range(15):
+        u_next, b, _, _ = oracle.rl_iterate(H, d, u, 1e-6)
+        nll = np.sum(b - d * np.log(b))
+        assert nll <= prev + 1e-9 * abs(prev if np.isfinite(prev) else 1)
+        prev = nll
+        u = u_next
+
+
+def test_rl_separable_slices():
+    # a PSF that is a delta along z decouples the slices: 3D RL == 2D RL per slice
+    shape = (3, 8, 10)
+    r = np.random.default_rng(31)
+    d = r.uniform(1, 20, shape)
+    p2 = r.uniform(0.1, 1, shape[1:])
+    psf = np.zeros(shape)
+    psf[shape[0] // 2] = p2
+    u3 = oracle.rl(d, psf, 5, 1e-6)
+    for z in range(shape[0]):
+        u2 = oracle.rl(d[z:z + 1], p2[None], 5, 1e-6)
+        assert np.allclose(u3[z], u2[0], rtol=1e-11)
+
+
+def test_rl_iterate_intermediates():
+    shape = (4, 5, 6)
+    r = np.random.default_rng(41)
+    d = r.uniform(1, 9, shape)
+    psf = r.uniform(size=shape)
+    H = oracle.psf_spectrum(psf)
+    u = r.uniform(1, 2, shape)
+    un, b, rr, q = oracle.rl_iterate(H, d, u, 1e-6)
+    h0 = oracle.center_to_origin(psf)
+    flip = h0[tuple(np.ix_(*[(-np.arange(n)) % n for n in shape]))]
+    assert np.allclose(b, direct_circular_conv(h0, u), rtol=1e-12)
+    assert np.allclose(rr, d / b, rtol=1e-12)
+    assert np.allclose(q, direct_circular_conv(flip, rr), rtol=1e-12)
+    assert np.allclose(un, u * q, rtol=1e-12)
+    # clamp: a tiny b is replaced by eps
+    d2 = np.ones(shape)
+    u2 = np.zeros(shape)
+    _, b2, r2, _ = oracle.rl_iterate(H, d2, u2, 0.5)
+    assert np.allclose(b2, 0.0) and np.allclose(r2, 2.0)
+
+
+# ----------------------------------------------------------- Gaussian PSF
+
+def test_psf_gaussian_closed_form():
+    shape = (9, 12, 11)
+    sxy, sz, A = 1.7, 2.6, 1.3
+    p = oracle.psf_gaussian(shape, sxy, sz, A)
+    c = (4, 6, 5)
+    assert np.isclose(p.sum(), A, rtol=1e-14)
+    assert np.unravel_index(np.argmax(p), shape) == c
+    assert np.isclose(p[4, 6, 6] / p[c], np.exp(-1 / (2 * sxy ** 2)), rtol=1e-14)
+    assert np.isclose(p[4, 8, 5] / p[c], np.exp(-4 / (2 * sxy ** 2)), rtol=1e-14)
+    assert np.isclose(p[6, 6, 5] / p[c], np.exp(-4 / (2 * sz ** 2)), rtol=1e-14)
+    assert np.isclose(p[3, 7, 4] / p[c], np.exp(-2 / (2 * sxy ** 2) - 1 / (2 * sz ** 2)), rtol=1e-14)
+    # centred => circularly symmetric about the origin after the shift => real spectrum
+    H = oracle.psf_spectrum(oracle.psf_gaussian((8, 10, 6), sxy, sz, A))
+    assert np.abs(H.imag).max() < 1e-14
+
+
+def test_psf_gaussian_grad_fd():
+    shape = (5, 7, 6)
+    theta = np.array([1.4, 2.1, 0.8])
+    w = np.random.default_rng(51).standard_normal(shape)
+
+    def L(t):
+        return np.sum(w * oracle.psf_gaussian(shape, *t))
+
+    g = oracle.psf_gaussian_grad(shape, *theta, w)
+    h = 1e-3
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = h
+        fd = (L(theta + e) - L(theta - e)) / (2 * h)
+        assert np.isclose(g[i], fd, rtol=1e-5, atol=1e-9)
+
+
+# -------------------------------------------------------------- gradient
+
+def _loss_parts(shape, seed):
+    r = np.random.default_rng(seed)
+    d = r.uniform(2.0, 20.0, shape)
+    xt = r.uniform(2.0, 20.0, shape)
+    return d, xt
+
+
+def test_rl_grad_image_fd():
+    shape = (4, 5, 6)
+    d, xt = _loss_parts(shape, 61)
+    psf = oracle.psf_gaussian(shape, 1.1, 1.6)
+    K, eps = 4, 1e-6
+
+    def L(dd):
+        u = oracle.rl(dd, psf, K, eps)
+        return np.mean((u - xt) ** 2)
+
+    u = oracle.rl(d, psf, K, eps)
+    g_out = 2 * (u - xt) / u.size
+    gd, _ = oracle.rl_grad(d, psf, K, eps, g_out)
+    r = np.random.default_rng(62)
+    h = 1e-3
+    for _ in range(3):
+        v = r.standard_normal(shape)
+        fd = (L(d + h * v) - L(d - h * v)) / (2 * h)
+        an = np.sum(gd * v)
+        assert np.isclose(an, fd, rtol=1e-5, atol=1e-10)
+    # single-voxel directions exercise the per-voxel terms
+    for idx in [(0, 0, 0), (2, 3, 1), (3, 4, 5)]:
+        v = np.zeros(shape)
+        v[idx] = 1.0
+        fd = (L(d + h * v) - L(d - h * v)) / (2 * h)
+        assert np.isclose(gd[idx], fd, rtol=1e-5, atol=1e-10)
+
+
+def test_rl_grad_psf_fd():
+    shape = (5, 4, 6)
+    d, xt = _loss_parts(shape, 71)
+    r = np.random.default_rng(72)
+    psf = r.uniform(0.2, 1.0, shape)            # not symmetric: exercises both correlation terms
+    psf /= psf.sum()
+    K, eps = 3, 1e-6
+
+    def L(p):
+        return np.mean((oracle.rl(d, p, K, eps) - xt) ** 2)
+
+    u = oracle.rl(d, psf, K, eps)
+    _, gp = oracle.rl_grad(d, psf, K, eps, 2 * (u - xt) / u.size)
+    h = 1e-6                                    # PSF entries are ~1e-2; error falls as h^2
+    for _ in range(3):
+        v = r.standard_normal(shape)
+        fd = (L(psf + h * v) - L(psf - h * v)) / (2 * h)
+        assert np.isclose(np.sum(gp * v), fd, rtol=1e-5, atol=1e-10)
+    # scale invariance => the gradient is orthogonal to the PSF itself
+    assert abs(np.sum(gp * psf)) <= 1e-10 * np.abs(gp).sum() * np.abs(psf).max() + 1e-14
+
+
+def test_rl_grad_params_fd():
+    # end to end: d L / d(sigma_xy, sigma_z, A) through the Gaussian PSF and RL
+    shape = (6, 8, 8)
+    d, xt = _loss_parts(shape, 81)
+    theta = np.array([1.3, 1.9, 1.0])
+    K, eps = 3, 1e-6
+
+    def L(t):
+        return np.mean((oracle.rl(d, oracle.psf_gaussian(shape, *t), K, eps) - xt) ** 2)
+
+    psf = oracle.psf_gaussian(shape, *theta)
+    u = oracle.rl(d, psf, K, eps)
+    _, gp = oracle.rl_grad(d, psf, K, eps, 2 * (u - xt) / u.size)
+    g = oracle.psf_gaussian_grad(shape, *theta, gp)
+    h = 1e-3
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = h
+        fd = (L(theta + e) - L(theta - e)) / (2 * h)
+        assert np.isclose(g[i], fd, rtol=1e-5, atol=1e-11)
+    assert abs(g[2]) < 1e-10        # RL is invariant to the PSF amplitude
+
+
+def test_rl_grad_zero_iterations():
+    # n_iter = 0: u = mean(d) everywhere, so dL/dd_i = sum(g_out) / V
+    shape = (3, 4, 5)
+    d, _ = _loss_parts(shape, 91)
+    g = np.random.default_rng(92).standard_normal(shape)
+    gd, gp = oracle.rl_grad(d, np.ones(shape) / 60, 0, 1e-6, g)
+    assert np.allclose(gd, g.sum() / g.size)
+    assert np.allclose(gp, 0.0)
