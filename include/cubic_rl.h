@@ -1,0 +1,130 @@
+/*
+ * cubic_rl.h -- C ABI of the GB300 (sm_103a) 3D Richardson-Lucy deconvolution library.
+ *
+ * The operation is the Richardson-Lucy iteration of arXiv 2510.14143, Section 4
+ * ("Richardson-Lucy deconvolution"): each iteration convolves the estimate with the
+ * PSF, divides the observed image by that blurred estimate, correlates the ratio with
+ * the PSF (convolution with the flipped PSF) and multiplies the estimate by the result.
+ * The same section fixes the PSF to the image's ZYX size and does the convolutions with
+ * FFTs.  Readings taken where the paper is silent:
+ *   - boundaries are circular (same-size FFT convolution, no padding);
+ *   - the PSF peak sits at index floor(n/2) on every axis;
+ *   - the initial estimate is the constant max(mean(image), eps);
+ *   - the ratio's denominator is clamped: image / max(blurred, eps).
+ *
+ * Conventions shared by every call:
+ *   - Volumes are float32, C-order [nz][ny][nx] (x fastest), dense, in device memory,
+ *     16-byte aligned.  dims[] is always {nz, ny, nx}.
+ *   - Every axis length must be one the library has kernels for: the 5-smooth
+ *     lengths (2^a 3^b 5^c) listed by cubic_rl_supported_length(); others give
+ *     CUBIC_ERR_UNSUPPORTED_SIZE.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *     validate their arguments on the host, then enqueue work on `stream` and return
+ *     without synchronising; results are ready when the stream reaches that point.
+ *   - On any error nothing is enqueued, the status is returned and a thread-local
+ *     message is available from cubic_last_error().  Nothing aborts or prints.
+ *   - A plan is used by one stream at a time (its scratch is shared by its calls).
+ */
+#ifndef CUBIC_RL_H
+#define CUBIC_RL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CUBIC_API __attribute__((visibility("default")))
+#else
+#define CUBIC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CUBIC_OK = 0,
+    CUBIC_ERR_INVALID_ARG = 1,
+    CUBIC_ERR_UNSUPPORTED_SIZE = 2,
+    CUBIC_ERR_ALIGNMENT = 3,
+    CUBIC_ERR_OUT_OF_MEMORY = 4,
+    CUBIC_ERR_CUDA = 5,
+    CUBIC_ERR_TIMEOUT = 6,
+    CUBIC_ERR_NOT_READY = 7
+} cubic_status_t;
+
+typedef struct cubic_rl_plan_s *cubic_rl_plan_t;
+
+/* Human-readable name of a status code (static string). */
+CUBIC_API const char *cubic_status_string(cubic_status_t s);
+
+/* Detail of the last error raised on the calling host thread (thread-local, static
+ * storage; valid until the next failing call on this thread). */
+CUBIC_API const char *cubic_last_error(void);
+
+/* 1 if an axis of length n is supported, else 0. */
+CUBIC_API int cubic_rl_supported_length(int64_t n);
+
+/* Create a plan for volumes of size dims = {nz, ny, nx} and PSF `psf` (device float32
+ * [nz][ny][nx], peak at (nz/2, ny/2, nx/2), floor division).  Section 4 of the paper:
+ * "Both the image and the PSF have the same ZYX size".  The plan moves the PSF peak to
+ * the origin and keeps H = DFT3(psf shifted) / V (complex64, [nz][ny][nx/2+1] padded),
+ * plus twiddle tables; the caller keeps owning `psf` and may free it once the stream
+ * has passed this call.  flags: reserved, pass 0.
+ * Errors: INVALID_ARG (null pointers, flags), UNSUPPORTED_SIZE, ALIGNMENT,
+ * OUT_OF_MEMORY, CUDA. */
+CUBIC_API cubic_status_t cubic_rl_plan(cubic_rl_plan_t *plan, const int64_t dims[3], const float *psf,
+                             unsigned flags, void *stream);
+
+/* Replace the PSF of an existing plan (same dims) -- e.g. after a PSF-parameter step. */
+CUBIC_API cubic_status_t cubic_rl_plan_update_psf(cubic_rl_plan_t plan, const float *psf, void *stream);
+
+/* Release a plan and everything it allocated (synchronises the device first). */
+CUBIC_API cubic_status_t cubic_rl_plan_destroy(cubic_rl_plan_t plan);
+
+/* Bytes of device scratch one deconvolution call of this plan needs (the complex
+ * half-spectrum work array). */
+CUBIC_API cubic_status_t cubic_rl_workspace_bytes(cubic_rl_plan_t plan, size_t *bytes);
+
+/* Give the plan caller-owned device scratch of at least cubic_rl_workspace_bytes()
+ * bytes (256-byte aligned).  Without it the plan allocates its own on first use.
+ * The caller must keep the memory alive while the plan uses it. */
+CUBIC_API cubic_status_t cubic_rl_set_workspace(cubic_rl_plan_t plan, void *dev_ptr, size_t bytes);
+
+/* Richardson-Lucy deconvolution, Section 4 of the paper: n_iter iterations of
+ *   b = psf (*) u;  r = image / max(b, eps);  q = psf (*)^T r;  u = u * q
+ * from u0 = max(mean(image), eps), (*) circular convolution, (*)^T its adjoint
+ * (correlation, i.e. convolution with the flipped PSF).
+ * image: device float32 [nz][ny][nx] (read only).  out: device float32 [nz][ny][nx],
+ * receives u_{n_iter}; must not overlap image.  n_iter >= 0 (0 gives u0).  eps > 0,
+ * finite.  Errors: INVALID_ARG, ALIGNMENT, OUT_OF_MEMORY (workspace), CUDA. */
+CUBIC_API cubic_status_t cubic_rl_deconvolve(cubic_rl_plan_t plan, const float *image, int n_iter, float eps,
+                                   float *out, void *stream);
+
+/* ---- building blocks (the same kernels, exposed for the forward model and for tests) ---- */
+
+/* Circular convolution with the plan's PSF (Section 4 of the paper, "forward
+ * convolution with the PSF"): out = psf (*) in.  flipped != 0 gives the correlation
+ * with the PSF ("back-convolution with the flipped PSF"), the adjoint of the former.
+ * in, out: device float32 [nz][ny][nx]; they may alias.  Uses the plan workspace. */
+CUBIC_API cubic_status_t cubic_rl_convolve(cubic_rl_plan_t plan, const float *in, int flipped, float *out,
+                                 void *stream);
+
+/* Layout of the plan's half spectra: xh = nx/2+1 valid columns, row pitch xp >= xh
+ * (complex64 elements); a spectrum is complex64 [nz][ny][xp]. */
+CUBIC_API cubic_status_t cubic_rl_spectrum_layout(cubic_rl_plan_t plan, int64_t *xh, int64_t *xp);
+
+/* Unnormalised forward 3D DFT, X[k] = sum_n x[n] exp(-2 pi i k.n / N), of a real volume
+ * (device float32 [nz][ny][nx]) into a half spectrum (device complex64 [nz][ny][xp],
+ * columns >= xh untouched).  `in` must not overlap `spec`. */
+CUBIC_API cubic_status_t cubic_rl_fft3_forward(cubic_rl_plan_t plan, const float *in, void *spec, void *stream);
+
+/* Inverse 3D DFT with the 1/V factor of a half spectrum back to a real volume.  The
+ * imaginary parts of the self-conjugate x-bins (kx = 0 and kx = nx/2) are ignored, as in
+ * any complex-to-real transform.  `spec` is overwritten (used as scratch). */
+CUBIC_API cubic_status_t cubic_rl_fft3_inverse(cubic_rl_plan_t plan, void *spec, float *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUBIC_RL_H */

@@ -1,0 +1,218 @@
+"""GB300 (sm_103a) 3D Richardson-Lucy deconvolution: thin Python binding.
+
+Every function here has the name of the C ABI call it wraps
+(``include/cubic_rl.h``) and only marshals arguments: torch tensors become
+device pointers, ``torch.cuda`` streams become ``cudaStream_t`` handles, and a
+non-zero status becomes a ``CubicError``.  All arithmetic runs in the CUDA
+kernels of ``libcubic_rl.so``; there is no CPU fallback.  If the library has
+not been built, every call raises.
+
+The method is Section 4 of arXiv 2510.14143 ("Richardson-Lucy
+deconvolution"): forward convolution with the PSF, ratio with the observed
+image, back-convolution with the flipped PSF, multiplicative update.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcubic_rl.so")
+
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {
+    0: "CUBIC_OK", 1: "CUBIC_ERR_INVALID_ARG", 2: "CUBIC_ERR_UNSUPPORTED_SIZE", 3: "CUBIC_ERR_ALIGNMENT",
+    4: "CUBIC_ERR_OUT_OF_MEMORY", 5: "CUBIC_ERR_CUDA", 6: "CUBIC_ERR_TIMEOUT", 7: "CUBIC_ERR_NOT_READY",
+}
+
+
+class CubicError(RuntimeError):
+    def __init__(self, status: int, call: str, detail: str):
+        self.status = status
+        super().__init__(f"{call} failed: {STATUS.get(status, status)}: {detail}")
+
+
+_vp, _i64, _ci, _cf, _sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+_SIGS = {
+    "cubic_status_string": ([_ci], ctypes.c_char_p),
+    "cubic_last_error": ([], ctypes.c_char_p),
+    "cubic_rl_supported_length": ([_i64], _ci),
+    "cubic_rl_plan": ([ctypes.POINTER(_vp), ctypes.POINTER(_i64), _vp, ctypes.c_uint, _vp], _ci),
+    "cubic_rl_plan_update_psf": ([_vp, _vp, _vp], _ci),
+    "cubic_rl_plan_destroy": ([_vp], _ci),
+    "cubic_rl_workspace_bytes": ([_vp, ctypes.POINTER(_sz)], _ci),
+    "cubic_rl_set_workspace": ([_vp, _vp, _sz], _ci),
+    "cubic_rl_deconvolve": ([_vp, _vp, _ci, _cf, _vp, _vp], _ci),
+    "cubic_rl_convolve": ([_vp, _vp, _ci, _vp, _vp], _ci),
+    "cubic_rl_spectrum_layout": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _ci),
+    "cubic_rl_fft3_forward": ([_vp, _vp, _vp, _vp], _ci),
+    "cubic_rl_fft3_inverse": ([_vp, _vp, _vp, _vp], _ci),
+}
+
+
+def lib():
+    """The loaded ``libcubic_rl.so`` (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_2510_14143_gb300.build`")
+            l = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(l, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = l
+    return _lib
+
+
+def _check(status: int, call: str) -> None:
+    if status != 0:
+        raise CubicError(status, call, lib().cubic_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (checked dtype/size), or an int address."""
+    if isinstance(t, int):
+        return t
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+class Plan:
+    """Owning wrapper of a ``cubic_rl_plan_t``; destroyed with the object."""
+
+    def __init__(self, handle: int, dims):
+        self.handle = handle
+        self.dims = tuple(int(d) for d in dims)
+        self.voxels = self.dims[0] * self.dims[1] * self.dims[2]
+
+    def close(self):
+        if self.handle:
+            lib().cubic_rl_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cubic_status_string(status: int) -> str:
+    return lib().cubic_status_string(status).decode()
+
+
+def cubic_last_error() -> str:
+    return lib().cubic_last_error().decode(errors="replace")
+
+
+def cubic_rl_supported_length(n: int) -> bool:
+    return bool(lib().cubic_rl_supported_length(int(n)))
+
+
+def cubic_rl_plan(dims, psf, flags: int = 0, stream=None) -> Plan:
+    """Plan for volumes of shape dims = (nz, ny, nx) with PSF `psf` (float32, same shape)."""
+    import torch
+    dims = tuple(int(d) for d in dims)
+    d = (_i64 * 3)(*dims)
+    h = _vp()
+    _check(lib().cubic_rl_plan(ctypes.byref(h), d, _ptr(psf, torch.float32, dims[0] * dims[1] * dims[2], "psf"),
+                               flags, _stream(stream)), "cubic_rl_plan")
+    return Plan(h.value, dims)
+
+
+def cubic_rl_plan_update_psf(plan: Plan, psf, stream=None) -> None:
+    import torch
+    _check(lib().cubic_rl_plan_update_psf(plan.handle, _ptr(psf, torch.float32, plan.voxels, "psf"),
+                                          _stream(stream)), "cubic_rl_plan_update_psf")
+
+
+def cubic_rl_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def cubic_rl_workspace_bytes(plan: Plan) -> int:
+    n = _sz()
+    _check(lib().cubic_rl_workspace_bytes(plan.handle, ctypes.byref(n)), "cubic_rl_workspace_bytes")
+    return int(n.value)
+
+
+def cubic_rl_set_workspace(plan: Plan, workspace) -> None:
+    """Hand the plan caller-owned scratch (a CUDA tensor kept alive by the plan object)."""
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().cubic_rl_set_workspace(plan.handle, _ptr(workspace, name="workspace"), nbytes),
+           "cubic_rl_set_workspace")
+    plan._workspace = workspace
+
+
+def cubic_rl_deconvolve(plan: Plan, image, n_iter: int, eps: float, out, stream=None) -> None:
+    import torch
+    _check(lib().cubic_rl_deconvolve(plan.handle, _ptr(image, torch.float32, plan.voxels, "image"), int(n_iter),
+                                     float(eps), _ptr(out, torch.float32, plan.voxels, "out"), _stream(stream)),
+           "cubic_rl_deconvolve")
+
+
+def cubic_rl_convolve(plan: Plan, x, flipped: bool, out, stream=None) -> None:
+    import torch
+    _check(lib().cubic_rl_convolve(plan.handle, _ptr(x, torch.float32, plan.voxels, "in"), int(bool(flipped)),
+                                   _ptr(out, torch.float32, plan.voxels, "out"), _stream(stream)),
+           "cubic_rl_convolve")
+
+
+def cubic_rl_spectrum_layout(plan: Plan):
+    xh, xp = _i64(), _i64()
+    _check(lib().cubic_rl_spectrum_layout(plan.handle, ctypes.byref(xh), ctypes.byref(xp)),
+           "cubic_rl_spectrum_layout")
+    return int(xh.value), int(xp.value)
+
+
+def _spec_numel(plan: Plan) -> int:
+    _, xp = cubic_rl_spectrum_layout(plan)
+    return plan.dims[0] * plan.dims[1] * xp
+
+
+def cubic_rl_fft3_forward(plan: Plan, x, spec, stream=None) -> None:
+    import torch
+    _check(lib().cubic_rl_fft3_forward(plan.handle, _ptr(x, torch.float32, plan.voxels, "in"),
+                                       _ptr(spec, torch.complex64, _spec_numel(plan), "spec"), _stream(stream)),
+           "cubic_rl_fft3_forward")
+
+
+def cubic_rl_fft3_inverse(plan: Plan, spec, out, stream=None) -> None:
+    import torch
+    _check(lib().cubic_rl_fft3_inverse(plan.handle, _ptr(spec, torch.complex64, _spec_numel(plan), "spec"),
+                                       _ptr(out, torch.float32, plan.voxels, "out"), _stream(stream)),
+           "cubic_rl_fft3_inverse")
+
+
+def rl_deconvolve(image, psf, n_iter: int, eps: float = 1e-6, out=None, stream=None):
+    """Convenience: plan + deconvolve for one volume (float32 CUDA tensors of one shape)."""
+    import torch
+    plan = cubic_rl_plan(image.shape, psf, 0, stream)
+    if out is None:
+        out = torch.empty_like(image)
+    cubic_rl_deconvolve(plan, image, n_iter, eps, out, stream)
+    out._cubic_plan = plan  # keep the plan (and its buffers) alive until out dies
+    return out

@@ -1,0 +1,273 @@
+// passes.cuh -- the three axis passes of the 3D real FFT convolution, with the
+// Richardson-Lucy pointwise steps fused into them.
+//
+// Data layout in HBM (all C-order, x fastest):
+//   real volumes   float  [nz][ny][nx]
+//   spectrum       float2 [nz][ny][xp]   xp >= nx/2+1, columns >= nx/2+1 unused
+//   PSF spectrum H float2 [nz][ny][xp]   same layout, already scaled by 1/V
+//
+// X pass  -- one CTA row-group owns complete x-lines.  Two real rows (2m, 2m+1)
+//            are packed as one complex line z = row0 + i row1; one complex FFT
+//            of length nx then gives both half spectra:
+//              A[k] = (Z[k] + conj Z[N-k]) / 2,  B[k] = (Z[k] - conj Z[N-k]) / (2i).
+//            The inverse packs Z[k] = A[k] + i B[k] (using A[N-k] = conj A[k]).
+//            The pointwise Richardson-Lucy steps run between the inverse and
+//            the forward transform of the same line (Section 4 of the paper:
+//            ratio with the observed image, multiplicative update).
+// Y pass  -- a CTA owns B adjacent spectrum columns x full y-lines (strided by xp).
+// Z pass  -- a CTA owns B adjacent columns x full z-lines; forward z FFT,
+//            pointwise product with H (forward convolution) or conj(H)
+//            (correlation = convolution with the flipped PSF), inverse z FFT.
+#pragma once
+
+#include "fft_core.cuh"
+
+namespace cubic {
+
+enum XMode : int {
+    XM_FWD = 0,     // real rows (src)            -> spectrum
+    XM_INV = 1,     // spectrum                   -> real rows (dst)
+    XM_RATIO = 2,   // spectrum -> b; r = d / max(b, eps)      -> spectrum of r
+    XM_UPDATE = 3,  // spectrum -> q; u = u * q (stored)       -> spectrum of u
+    XM_FINAL = 4,   // spectrum -> q; out = u * q
+    XM_COUNT = 5
+};
+
+struct XArgs {
+    const float2 *spec_in;
+    float2 *spec_out;
+    const float *src;  // XM_FWD input rows
+    float *dst;        // XM_INV output rows, XM_FINAL output
+    float *u;          // estimate (XM_UPDATE read/write, XM_FINAL read)
+    const float *d;    // observed image (XM_RATIO)
+    const float2 *tw;  // twiddles of length nx
+    int64_t rows;      // nz * ny
+    int64_t xp;        // spectrum pitch (complex elements)
+    float eps;
+};
+
+struct YArgs {
+    float2 *spec;
+    const float2 *tw;
+    int64_t nz;
+    int64_t xh;  // nx/2 + 1 valid columns
+    int64_t xp;
+    int inverse;
+};
+
+enum ZMode : int { ZM_FWD_SCALE = 0, ZM_CONV = 1, ZM_CORR = 2, ZM_INV_SCALE = 3 };
+
+struct ZArgs {
+    float2 *spec;
+    const float2 *H;
+    const float2 *tw;
+    int64_t ny;
+    int64_t xh;
+    int64_t xp;
+    int mode;
+    float scale;  // ZM_FWD_SCALE / ZM_INV_SCALE only
+};
+
+// ------------------------------------------------------------------ X pass
+
+struct SmemPadded {  // element pos at base[pos + pos/32]
+    float2 *base;
+    __device__ __forceinline__ float2 &at(int pos) const { return base[pos + (pos >> 5)]; }
+};
+
+struct SmemStrided {  // element pos at base[pos * stride]
+    float2 *base;
+    int stride;
+    __device__ __forceinline__ float2 &at(int pos) const { return base[pos * stride]; }
+};
+
+template <int N>
+constexpr int x_smem_line() { return N + (N >> 5) + 1; }
+
+template <int N, int P, int L, int MODE>
+__global__ void __launch_bounds__(P * L) k_xpass(XArgs a)
+{
+    constexpr int E = N / P;
+    extern __shared__ float2 smem_x[];
+    const int t = threadIdx.x % P;
+    const int l = threadIdx.x / P;
+    const int64_t m = (int64_t)blockIdx.x * L + l;
+    const int64_t r0 = 2 * m, r1 = 2 * m + 1;
+    const bool ok0 = r0 < a.rows, ok1 = r1 < a.rows;
+    SmemPadded sm{smem_x + l * x_smem_line<N>()};
+    auto sync = [] { __syncthreads(); };
+    using FFT = LineFFT<N, P>;
+
+    float2 v[E];
+    if constexpr (MODE == XM_FWD) {
+        const float *s0 = a.src + r0 * N, *s1 = a.src + r1 * N;
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            const int n = t + P * i;
+            v[i] = make_float2(ok0 ? __ldg(s0 + n) : 0.f, ok1 ? __ldg(s1 + n) : 0.f);
+        });
+    } else {
+        const float2 *q0 = a.spec_in + r0 * a.xp, *q1 = a.spec_in + r1 * a.xp;
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            const int k = t + P * i;
+            const bool hi = 2 * k > N;
+            const int kk = hi ? N - k : k;
+            float2 A = ok0 ? q0[kk] : make_float2(0.f, 0.f);
+            float2 B = ok1 ? q1[kk] : make_float2(0.f, 0.f);
+            if (hi) {
+                A.y = -A.y;
+                B.y = -B.y;
+            }
+            if (k == 0 || 2 * k == N) {  // self-conjugate bins of a real line
+                A.y = 0.f;
+                B.y = 0.f;
+            }
+            v[i] = make_float2(A.x - B.y, A.y + B.x);  // A + i B
+        });
+        FFT::inverse(v, sm, a.tw, t, sync);
+
+        // pointwise step on the real rows (v.x = row r0, v.y = row r1)
+        if constexpr (MODE == XM_INV) {
+            float *o0 = a.dst + r0 * N, *o1 = a.dst + r1 * N;
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                const int n = t + P * i;
+                if (ok0) o0[n] = v[i].x;
+                if (ok1) o1[n] = v[i].y;
+            });
+        } else if constexpr (MODE == XM_RATIO) {
+            const float *d0 = a.d + r0 * N, *d1 = a.d + r1 * N;
+            const float eps = a.eps;
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                const int n = t + P * i;
+                const float x0 = ok0 ? __fdiv_rn(__ldg(d0 + n), fmaxf(v[i].x, eps)) : 0.f;
+                const float x1 = ok1 ? __fdiv_rn(__ldg(d1 + n), fmaxf(v[i].y, eps)) : 0.f;
+                v[i] = make_float2(x0, x1);
+            });
+        } else if constexpr (MODE == XM_UPDATE || MODE == XM_FINAL) {
+            float *u0 = a.u + r0 * N, *u1 = a.u + r1 * N;
+            float *o0 = (MODE == XM_UPDATE ? a.u : a.dst) + r0 * N;
+            float *o1 = (MODE == XM_UPDATE ? a.u : a.dst) + r1 * N;
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                const int n = t + P * i;
+                const float x0 = ok0 ? u0[n] * v[i].x : 0.f;
+                const float x1 = ok1 ? u1[n] * v[i].y : 0.f;
+                if (ok0) o0[n] = x0;
+                if (ok1) o1[n] = x1;
+                v[i] = make_float2(x0, x1);
+            });
+        }
+    }
+
+    if constexpr (MODE == XM_FWD || MODE == XM_RATIO || MODE == XM_UPDATE) {
+        FFT::forward(v, sm, a.tw, t, sync);
+        // split the packed spectrum into the two rows' half spectra
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            sm.at(t + P * i) = v[i];
+        });
+        sync();
+        float2 *q0 = a.spec_out + r0 * a.xp, *q1 = a.spec_out + r1 * a.xp;
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            const int k = t + P * i;
+            if (2 * k <= N) {
+                const float2 zk = v[i];
+                const float2 zn = sm.at(k == 0 ? 0 : N - k);
+                const float2 A = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+                const float2 B = make_float2(0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x));
+                if (ok0) q0[k] = A;
+                if (ok1) q1[k] = B;
+            }
+        });
+    }
+}
+
+// ------------------------------------------------------------------ Y pass
+
+template <int N, int P, int B>
+__global__ void __launch_bounds__(P * B) k_ypass(YArgs a)
+{
+    constexpr int E = N / P;
+    extern __shared__ float2 smem_y[];
+    const int b = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int64_t col = (int64_t)blockIdx.x * B + b;
+    const bool ok = col < a.xh;
+    float2 *base = a.spec + (int64_t)blockIdx.y * N * a.xp + col;
+    SmemStrided sm{smem_y + b, B};
+    auto sync = [] { __syncthreads(); };
+    float2 v[E];
+    const float sgn = a.inverse ? -1.f : 1.f;
+    static_for<0, E>([&](auto i_) {
+        constexpr int i = CUBIC_CI(i_);
+        float2 x = ok ? base[(int64_t)(t + P * i) * a.xp] : make_float2(0.f, 0.f);
+        v[i] = make_float2(x.x, sgn * x.y);
+    });
+    LineFFT<N, P>::forward(v, sm, a.tw, t, sync);
+    if (ok) {
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            base[(int64_t)(t + P * i) * a.xp] = make_float2(v[i].x, sgn * v[i].y);
+        });
+    }
+}
+
+// ------------------------------------------------------------------ Z pass
+
+template <int N, int P, int B>
+__global__ void __launch_bounds__(P * B) k_zpass(ZArgs a)
+{
+    constexpr int E = N / P;
+    extern __shared__ float2 smem_z[];
+    const int b = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    const int64_t col = (int64_t)blockIdx.x * B + b;
+    const bool ok = col < a.xh;
+    const int64_t zstride = a.ny * a.xp;
+    const int64_t off = (int64_t)blockIdx.y * a.xp + col;
+    float2 *base = a.spec + off;
+    SmemStrided sm{smem_z + b, B};
+    auto sync = [] { __syncthreads(); };
+    using FFT = LineFFT<N, P>;
+    float2 v[E];
+    const bool inv_only = a.mode == ZM_INV_SCALE;
+    static_for<0, E>([&](auto i_) {
+        constexpr int i = CUBIC_CI(i_);
+        const float2 x = ok ? base[(int64_t)(t + P * i) * zstride] : make_float2(0.f, 0.f);
+        v[i] = inv_only ? cconj(x) : x;
+    });
+    FFT::forward(v, sm, a.tw, t, sync);
+    if (a.mode == ZM_FWD_SCALE || inv_only) {
+        const float s = a.scale, sy = inv_only ? -a.scale : a.scale;
+        if (ok) {
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                base[(int64_t)(t + P * i) * zstride] = make_float2(v[i].x * s, v[i].y * sy);
+            });
+        }
+        return;
+    }
+    const float2 *hb = a.H + off;
+    const bool corr = a.mode == ZM_CORR;
+    // product with H or conj(H), then conjugate for the inverse transform
+    static_for<0, E>([&](auto i_) {
+        constexpr int i = CUBIC_CI(i_);
+        const float2 h = ok ? __ldg(hb + (int64_t)(t + P * i) * zstride) : make_float2(0.f, 0.f);
+        const float2 p = corr ? cmulconj(v[i], h) : cmul(v[i], h);
+        v[i] = cconj(p);
+    });
+    sync();  // the forward transform's last shared-memory reads are done
+    FFT::forward(v, sm, a.tw, t, sync);
+    if (ok) {
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            base[(int64_t)(t + P * i) * zstride] = cconj(v[i]);
+        });
+    }
+}
+
+}  // namespace cubic

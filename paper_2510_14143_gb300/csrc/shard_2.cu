@@ -1,0 +1,3 @@
+// Kernel instantiations, build shard 2 (lengths with index % 8 == 2).
+#define CUBIC_SHARD 2
+#include "kernels_shard.cuh"

@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: the 3D FFTs and convolutions run in FP32 with FP64-generated
+twiddles; their relative L2 error against the FP64 oracle is bounded by a few
+units of FP32 rounding times log2(V) -- 1e-5 is used.  The full
+Richardson-Lucy estimate after 20 iterations must be within a relative L2 of
+1e-4 of the oracle (the stated precision target for the 64x64x32 workload).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_14143_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cr():
+    from paper_2510_14143_gb300 import build
+    build.build()
+    import paper_2510_14143_gb300 as m
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_forward(cr, x):
+    shape = x.shape
+    psf = np.zeros(shape, np.float32)
+    psf[tuple(n // 2 for n in shape)] = 1
+    plan = cr.cubic_rl_plan(shape, dev(psf))
+    xh, xp = cr.cubic_rl_spectrum_layout(plan)
+    spec = torch.zeros((shape[0], shape[1], xp), dtype=torch.complex64, device="cuda")
+    cr.cubic_rl_fft3_forward(plan, dev(x), spec)
+    torch.cuda.synchronize()
+    return plan, spec, xh
+
+
+LEN = synth.SMOOTH_48_160 + (1, 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32, 36, 40, 45,
+                             192, 256, 320, 384, 512, 640, 768, 1024)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("n", sorted(set(LEN)))
+def test_fft3_forward_every_length(cr, axis, n):
+    shape = [3, 2, 4]
+    shape[axis] = n
+    x = synth.random_field(tuple(shape), seed=n * 3 + axis, lo=-1, hi=1)
+    plan, spec, xh = gpu_forward(cr, x)
+    ref = oracle.fft3(x.astype(np.float64))[:, :, :xh]
+    got = spec.cpu().numpy()[:, :, :xh]
+    assert rel_l2(got, ref) < 1e-5
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 2), (2, 3, 4), (5, 9, 15), (32, 64, 64), (7, 5, 3),
+                                   (12, 160, 125), (6, 75, 81), (4, 8, 1024), (128, 6, 10)])
+def test_fft3_roundtrip_and_spectrum(cr, shape):
+    x = synth.random_field(shape, seed=sum(shape), lo=-1, hi=1)
+    plan, spec, xh = gpu_forward(cr, x)
+    ref = oracle.fft3(x.astype(np.float64))[:, :, :xh]
+    assert rel_l2(spec.cpu().numpy()[:, :, :xh], ref) < 1e-5
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    cr.cubic_rl_fft3_inverse(plan, spec, out)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), x) < 1e-5
+
+
+@pytest.mark.parametrize("shape", [(4, 6, 5), (5, 9, 15), (32, 64, 64), (16, 48, 75), (9, 27, 128)])
+@pytest.mark.parametrize("flipped", [False, True])
+def test_convolve_matches_oracle(cr, shape, flipped):
+    r = np.random.default_rng(sum(shape) + flipped)
+    psf = r.uniform(0.1, 1.0, shape).astype(np.float32)      # not symmetric
+    psf /= psf.sum()
+    x = synth.random_field(shape, seed=7 + sum(shape))
+    plan = cr.cubic_rl_plan(shape, dev(psf))
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    cr.cubic_rl_convolve(plan, dev(x), flipped, out)
+    torch.cuda.synchronize()
+    ref = oracle.convolve(oracle.psf_spectrum(psf.astype(np.float64)), x.astype(np.float64), flipped)
+    assert rel_l2(out.cpu().numpy(), ref) < 1e-5
+
+
+def run_rl(cr, d, psf, n_iter, eps=1e-6):
+    plan = cr.cubic_rl_plan(d.shape, dev(psf))
+    out = torch.empty(d.shape, dtype=torch.float32, device="cuda")
+    cr.cubic_rl_deconvolve(plan, dev(d), n_iter, eps, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_rl_small_workload_20_iterations(cr):
+    w = synth.SMALL
+    d, _ = synth.workload_volume(w)
+    psf = oracle.psf_gaussian(d.shape, w.psf_sigma_xy, w.psf_sigma_z).astype(np.float32)
+    got = run_rl(cr, d, psf, w.n_iter)
+    ref = oracle.rl(d, psf, w.n_iter, 1e-6)
+    err = rel_l2(got, ref)
+    print(f"rl 64x64x32, 20 it: rel-L2 = {err:.3e}")
+    assert err <= 1e-4
+
+
+@pytest.mark.parametrize("n_iter", [0, 1, 2, 5])
+def test_rl_few_iterations(cr, n_iter):
+    w = synth.SMALL
+    d, _ = synth.workload_volume(w)
+    psf = oracle.psf_gaussian(d.shape, w.psf_sigma_xy, w.psf_sigma_z).astype(np.float32)
+    got = run_rl(cr, d, psf, n_iter)
+    ref = oracle.rl(d, psf, n_iter, 1e-6)
+    assert rel_l2(got, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("shape", [(5, 9, 15), (3, 1, 8), (1, 16, 12), (27, 25, 18), (15, 81, 75)])
+def test_rl_ragged_shapes(cr, shape):
+    d, _ = synth.make_volume(shape, 3, (1.0, 2.0), 10.0, 1.2, 1.5, 4242 + sum(shape))
+    psf = oracle.psf_gaussian(shape, 1.2, 1.5).astype(np.float32)
+    got = run_rl(cr, d, psf, 6)
+    ref = oracle.rl(d, psf, 6, 1e-6)
+    assert rel_l2(got, ref) <= 1e-4
+
+
+def test_rl_asymmetric_psf(cr):
+    shape = (8, 20, 24)
+    r = np.random.default_rng(99)
+    psf = r.uniform(0.0, 1.0, shape).astype(np.float32) ** 4
+    psf /= psf.sum()
+    d = r.uniform(1, 50, shape).astype(np.float32)
+    got = run_rl(cr, d, psf, 8)
+    ref = oracle.rl(d, psf, 8, 1e-6)
+    assert rel_l2(got, ref) <= 1e-4
+
+
+def test_rl_clamp_active(cr):
+    # an image with large zero regions drives b below eps somewhere
+    shape = (8, 16, 16)
+    d = np.zeros(shape, np.float32)
+    d[2:4, 3:6, 4:9] = 100.0
+    psf = np.zeros(shape, np.float32)
+    psf[4, 8, 8] = 0.6
+    psf[4, 8, 9] = 0.4
+    eps = 1e-3
+    got = run_rl(cr, d, psf, 4, eps)
+    ref = oracle.rl(d, psf, 4, eps)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_rl_delta_psf_identity(cr):
+    shape = (16, 32, 48)
+    d = synth.random_field(shape, 5, 1.0, 100.0)
+    psf = np.zeros(shape, np.float32)
+    psf[8, 16, 24] = 1.0
+    got = run_rl(cr, d, psf, 3)
+    assert rel_l2(got, d) < 1e-6
+
+
+def test_rl_medium_workload_parity(cr):
+    # 256x256x128 at 10 iterations against the oracle (the full 100 are timed by the bench)
+    w = synth.MEDIUM
+    d, _ = synth.workload_volume(w)
+    psf = oracle.psf_gaussian(d.shape, w.psf_sigma_xy, w.psf_sigma_z).astype(np.float32)
+    got = run_rl(cr, d, psf, 10)
+    ref = oracle.rl(d, psf, 10, 1e-6)
+    err = rel_l2(got, ref)
+    print(f"rl 256x256x128, 10 it: rel-L2 = {err:.3e}")
+    assert err <= 1e-4
+
+
+def test_errors_are_reported(cr):
+    shape = (4, 4, 4)
+    psf = dev(np.ones(shape, np.float32) / 64)
+    plan = cr.cubic_rl_plan(shape, psf)
+    img = dev(np.ones(shape, np.float32))
+    with pytest.raises(cr.CubicError) as e:
+        cr.cubic_rl_deconvolve(plan, img, 1, 0.0, torch.empty_like(img))
+    assert e.value.status == 1
+    with pytest.raises(cr.CubicError) as e:
+        cr.cubic_rl_deconvolve(plan, img, -1, 1e-6, torch.empty_like(img))
+    assert e.value.status == 1
+    with pytest.raises(cr.CubicError) as e:
+        cr.cubic_rl_deconvolve(plan, img, 1, 1e-6, img)            # out aliases image
+    assert e.value.status == 1
+    big = torch.empty(65, dtype=torch.float32, device="cuda")
+    with pytest.raises(cr.CubicError) as e:
+        cr.cubic_rl_deconvolve(plan, img, 1, 1e-6, big[1:].view(4, 4, 4).data_ptr())  # misaligned
+    assert e.value.status == 3
+    with pytest.raises(cr.CubicError) as e:
+        cr.cubic_rl_plan((4, 4, 7), dev(np.ones((4, 4, 7), np.float32)))
+    assert e.value.status == 2
