@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of 3D Richardson-Lucy deconvolution on GB300.
+
+One step = one complete deconvolution of the workload volume (default
+1024x1024x128 float32, 50 iterations, Gaussian PSF sigma_xy 2.5 / sigma_z 6),
+i.e. every step of the hot path: flux sum and initial estimate, then per
+iteration forward convolution, ratio, flipped-PSF correlation and update.
+Metric: Gvoxel-iter/s = V * n_iter * steps / time / 1e9 (higher is better).
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and
+torch.cuda.synchronize() on both sides, timed with CUDA events on the stream
+the library launches on; the max over ranks is reported.  The inputs (512 MiB
+volume, 2.1 GiB working set) are larger than the 129 MB L2, so no flush is
+needed between steps.  Per-kernel device time comes from the library's own
+event pairs around each launch in the same timed region.
+
+Multi-GPU: a single volume does not shard, so ranks run independent replicas
+(weak scaling); the only collectives are the host-side barrier and the max of
+the elapsed time.
+
+--impl reference times the FP64 CPU oracle (the reference for this build) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_14143_gb300 import synth  # noqa: E402
+
+METRIC = "3D RL Gvoxel-iter/s"
+UNIT = "Gvoxel-iter/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_inputs(w: synth.Workload):
+    d, _ = synth.workload_volume(w)
+    return d
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args, w: synth.Workload):
+    import torch
+    import paper_2510_14143_gb300 as cr
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    shape, V, n_iter, eps = w.shape, w.voxels, w.n_iter, 1e-6
+    d_host = make_inputs(w)
+    d = torch.from_numpy(d_host).cuda()
+    psf = torch.empty(shape, dtype=torch.float32, device="cuda")
+    cr.cubic_psf_gaussian(shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0, psf)
+    plan = cr.cubic_rl_plan(shape, psf)
+    out = torch.empty_like(d)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        cr.cubic_rl_deconvolve(plan, d, n_iter, eps, out)
+    barrier()
+
+    # ---- device-resident timed region (per-kernel events inside)
+    cr.cubic_rl_profile(plan, True, max_events=2 * (n_iter * 8 + 8) * args.steps + 64)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        cr.cubic_rl_deconvolve(plan, d, n_iter, eps, out)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof = cr.cubic_rl_profile_read(plan)
+    cr.cubic_rl_profile(plan, False)
+    ms = max_over_ranks(ms)
+    flux_rel = abs(out.double().sum().item() / d.double().sum().item() - 1.0)
+
+    # ---- end to end through the host-buffer entry point
+    h_in = torch.from_numpy(d_host).pin_memory()
+    h_out = torch.empty(shape, dtype=torch.float32).pin_memory()
+    cr.cubic_rl_deconvolve_host(plan, h_in, n_iter, eps, h_out)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        cr.cubic_rl_deconvolve_host(plan, h_in, n_iter, eps, h_out)
+    e1.record(stream)
+    barrier()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+
+    units = V * n_iter * args.steps * world
+    value = units / (ms * 1e-3) / 1e9
+    e2e = units / (ms_e2e * 1e-3) / 1e9
+
+    # roofline of the kernel with the largest share of device time
+    kernels = {k: v for k, v in prof.items() if v["timed"] > 0}
+    top = max(kernels, key=lambda k: kernels[k]["ms"])
+    tk = kernels[top]
+    per_launch_bytes = tk["bytes"] / tk["launches"]
+    avg_s = tk["ms"] / tk["timed"] * 1e-3
+    peak, peak_src = hbm_peak()
+    achieved = per_launch_bytes / avg_s / 1e9
+    total_kernel_ms = sum(v["ms"] for v in kernels.values())
+    launches = sum(v["launches"] for v in prof.values())
+    traffic = load_traffic(top, w)
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "xyz": list(w.xyz), "n_iter": n_iter, "eps": eps,
+                   "psf_sigma_xy": w.psf_sigma_xy, "psf_sigma_z": w.psf_sigma_z,
+                   "l2": "inputs larger than L2 (volume 512 MiB, working set ~2.1 GiB vs 129 MB L2), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": V * 4, "d2h_bytes_per_step": V * 4},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "peak_source": peak_src,
+                     "bytes_per_launch": per_launch_bytes},
+        "model_84B_frac": round(value * 84.0 / peak, 4),
+        "kernels": {k: {"share": round(v["ms"] / total_kernel_ms, 4),
+                        "avg_us": round(v["ms"] / v["timed"] * 1e3, 2),
+                        "GBps": round(v["bytes"] / v["launches"] / (v["ms"] / v["timed"] * 1e-3) / 1e9, 1)}
+                    for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["ms"])},
+        "flux_rel_err": flux_rel,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w, d_host, args.cpu_sample)
+    if dist is not None:
+        dist.destroy_process_group()
+    return rank, result
+
+
+def load_traffic(kernel: str, w: synth.Workload):
+    """DRAM bytes per launch from the committed ncu summary, if it covers this kernel build."""
+    path = os.path.join(ROOT, "profiles", "ncu_dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src_hash = source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == w.name:
+            if parts[3] != src_hash:
+                return None
+            return float(parts[2])
+    return None
+
+
+def source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2510_14143_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:12]
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(w: synth.Workload, d_host, sample: str):
+    """A bounded sample of the workload for the FP64 oracle: (d, psf) of the sample."""
+    import oracle
+    if sample == "full":
+        dd = d_host
+    else:  # "crop": a 5-smooth sub-volume of the workload's own data
+        nz, ny, nx = w.shape
+        dd = d_host[:min(nz, 64), :min(ny, 256), :min(nx, 256)]
+    dd = np.ascontiguousarray(dd, dtype=np.float64)
+    psf = oracle.psf_gaussian(dd.shape, w.psf_sigma_xy, w.psf_sigma_z)
+    return dd, psf
+
+
+def cpu_baseline(w: synth.Workload, d_host, sample: str, iters: int = 1):
+    import oracle
+    dd, psf = oracle_sample(w, d_host, sample)
+    H = oracle.psf_spectrum(psf)                  # plan, excluded like the GPU plan
+    u = np.full(dd.shape, oracle.initial_value(dd, 1e-6))
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        u, _, _, _ = oracle.rl_iterate(H, dd, u, 1e-6)
+    dt = time.perf_counter() - t0
+    vox = dd.size
+    return {"value": round(vox * iters / dt / 1e9, 6), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{iters} RL iteration(s) of the FP64 oracle on a {dd.shape[2]}x{dd.shape[1]}x{dd.shape[0]} "
+                      f"{'volume' if sample == 'full' else 'crop'} of the workload (PSF spectrum precomputed), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, w: synth.Workload):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return rank, None
+    import oracle
+    d_host = make_inputs(w)
+    dd, psf = oracle_sample(w, d_host, args.cpu_sample)
+    H = oracle.psf_spectrum(psf)
+    u = np.full(dd.shape, oracle.initial_value(dd, 1e-6))
+    for _ in range(args.warmup):
+        u, _, _, _ = oracle.rl_iterate(H, dd, u, 1e-6)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, _, _, _ = oracle.rl_iterate(H, dd, u, 1e-6)
+    dt = time.perf_counter() - t0
+    value = dd.size * args.steps / dt / 1e9
+    sample = (f"one FP64 oracle RL iteration per step on a {dd.shape[2]}x{dd.shape[1]}x{dd.shape[0]} "
+              f"{'volume' if args.cpu_sample == 'full' else 'crop'} of the {w.name} workload")
+    result = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "xyz": list(w.xyz), "n_iter": w.n_iter, "eps": 1e-6},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return rank, result
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=sorted(synth.PLAIN), default=synth.LARGE.name)
+    ap.add_argument("--cpu-sample", choices=("crop", "full"), default="full")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = synth.PLAIN[args.workload]
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank, result = run_reference(args, w) if args.impl == "reference" else run_ours(args, w)
+    if rank == 0 and result is not None:
+        print(json.dumps(result), flush=True)
+
+
+if __name__ == "__main__":
+    main()

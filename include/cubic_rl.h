@@ -100,6 +100,75 @@ CUBIC_API cubic_status_t cubic_rl_set_workspace(cubic_rl_plan_t plan, void *dev_
 CUBIC_API cubic_status_t cubic_rl_deconvolve(cubic_rl_plan_t plan, const float *image, int n_iter, float eps,
                                    float *out, void *stream);
 
+/* cubic_rl_deconvolve on host buffers: copies `image` (host, V floats; pinned memory makes
+ * the copies asynchronous) to device memory owned by the plan, deconvolves there, and
+ * copies the estimate back into `out` (host, V floats).  All three steps are enqueued on
+ * `stream`; `out` is valid once the stream has passed this call.  The first call
+ * allocates the two device staging volumes (released with the plan). */
+CUBIC_API cubic_status_t cubic_rl_deconvolve_host(cubic_rl_plan_t plan, const float *image, int n_iter,
+                                                  float eps, float *out, void *stream);
+
+/* Normalised anisotropic Gaussian PSF, psf = amp * g / sum(g) with
+ * g = exp(-(dx^2 + dy^2) / (2 sigma_xy^2) - dz^2 / (2 sigma_z^2)), (dx, dy, dz) = index -
+ * floor(n/2) per axis.  The paper models its PSF with a theoretical (Richards-Wolf)
+ * model of the same ZYX size as the image (Section 4, "Dataset description"); this
+ * parametric stand-in is the one whose parameters the differentiable path fits.
+ * psf: device float32 [nz][ny][nx].  g in float32, sum(g) in double.  Uses a small
+ * stream-ordered scratch allocation.  Errors: INVALID_ARG, ALIGNMENT, CUDA. */
+CUBIC_API cubic_status_t cubic_psf_gaussian(const int64_t dims[3], float sigma_xy, float sigma_z, float amp,
+                                            float *psf, void *stream);
+
+/* Device-side status of the plan's kernels: synchronises `stream`, then returns
+ * CUBIC_ERR_TIMEOUT (and clears the flag) if any kernel's bounded wait on an asynchronous
+ * copy gave up since the last check, else CUBIC_OK.  Kernels that give up skip their
+ * stores, so their outputs are then undefined. */
+CUBIC_API cubic_status_t cubic_rl_stream_status(cubic_rl_plan_t plan, void *stream);
+
+/* ---- launch shapes and autotuning ---- */
+
+/* counts[3] = number of compiled launch-shape variants of the X, Y and Z passes for this
+ * plan's lengths; chosen[3] = the variants in use.  Either pointer may be NULL. */
+CUBIC_API cubic_status_t cubic_rl_plan_variants(cubic_rl_plan_t plan, int counts[3], int chosen[3]);
+
+/* Select launch-shape variants explicitly (INVALID_ARG if out of range).  Every variant
+ * computes the same transform; they differ in threads per line and lines per CTA. */
+CUBIC_API cubic_status_t cubic_rl_plan_set_variants(cubic_rl_plan_t plan, int vx, int vy, int vz);
+
+/* Process the Y-forward / Z / Y-inverse passes of each convolution in chunks of `columns`
+ * spectrum columns (a multiple of 16; 0 = all columns in one launch per pass), so that a
+ * chunk stays in L2 between the three passes.  Results do not depend on it. */
+CUBIC_API cubic_status_t cubic_rl_plan_set_chunk(cubic_rl_plan_t plan, int64_t columns);
+
+/* Current chunk setting (-1 for a NULL plan). */
+CUBIC_API int64_t cubic_rl_plan_chunk(cubic_rl_plan_t plan);
+
+/* Time every variant of each pass on this plan's own buffers (image read, `out` and the
+ * workspace overwritten) and keep the fastest.  Synchronises the stream several times, so
+ * do not call it while capturing a graph.  The choice is remembered for later plans of
+ * the same dims in this process and, if the environment variable CUBIC_TUNE_CACHE names a
+ * file, appended there and read back by later processes. */
+CUBIC_API cubic_status_t cubic_rl_autotune(cubic_rl_plan_t plan, const float *image, float *out,
+                                           void *stream);
+
+/* ---- launch accounting and per-kernel timing ---- */
+
+/* Number of kernel kinds and the name of each (static strings). */
+CUBIC_API int cubic_rl_kernel_kinds(void);
+CUBIC_API const char *cubic_rl_kernel_name(int kind);
+
+/* Reset the plan's launch counters; with enable != 0 also bracket every later launch by a
+ * pair of CUDA events on its stream (up to max_events events, taken from a pool the plan
+ * keeps), so that per-kernel device time can be read back.  Timing adds two event records
+ * per launch to the stream. */
+CUBIC_API cubic_status_t cubic_rl_profile(cubic_rl_plan_t plan, int enable, int max_events);
+
+/* Per kernel kind (arrays of n_kinds entries, any may be NULL): summed event-timed device
+ * time in ms and the number of timed launches (synchronises on the last recorded event),
+ * the number of launches enqueued since cubic_rl_profile() and their algorithmic HBM bytes
+ * (each array the kernel must read or write, counted once). */
+CUBIC_API cubic_status_t cubic_rl_profile_read(cubic_rl_plan_t plan, int n_kinds, double *total_ms,
+                                               int64_t *timed_launches, int64_t *launches, double *bytes);
+
 /* ---- building blocks (the same kernels, exposed for the forward model and for tests) ---- */
 
 /* Circular convolution with the plan's PSF (Section 4 of the paper, "forward

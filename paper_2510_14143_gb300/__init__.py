@@ -50,6 +50,19 @@ _SIGS = {
     "cubic_rl_spectrum_layout": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _ci),
     "cubic_rl_fft3_forward": ([_vp, _vp, _vp, _vp], _ci),
     "cubic_rl_fft3_inverse": ([_vp, _vp, _vp, _vp], _ci),
+    "cubic_rl_deconvolve_host": ([_vp, _vp, _ci, _cf, _vp, _vp], _ci),
+    "cubic_psf_gaussian": ([ctypes.POINTER(_i64), _cf, _cf, _cf, _vp, _vp], _ci),
+    "cubic_rl_stream_status": ([_vp, _vp], _ci),
+    "cubic_rl_plan_variants": ([_vp, ctypes.POINTER(_ci), ctypes.POINTER(_ci)], _ci),
+    "cubic_rl_plan_set_variants": ([_vp, _ci, _ci, _ci], _ci),
+    "cubic_rl_autotune": ([_vp, _vp, _vp, _vp], _ci),
+    "cubic_rl_plan_set_chunk": ([_vp, _i64], _ci),
+    "cubic_rl_plan_chunk": ([_vp], _i64),
+    "cubic_rl_kernel_kinds": ([], _ci),
+    "cubic_rl_kernel_name": ([_ci], ctypes.c_char_p),
+    "cubic_rl_profile": ([_vp, _ci, _ci], _ci),
+    "cubic_rl_profile_read": ([_vp, _ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64),
+                               ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)], _ci),
 }
 
 
@@ -172,6 +185,95 @@ def cubic_rl_deconvolve(plan: Plan, image, n_iter: int, eps: float, out, stream=
     _check(lib().cubic_rl_deconvolve(plan.handle, _ptr(image, torch.float32, plan.voxels, "image"), int(n_iter),
                                      float(eps), _ptr(out, torch.float32, plan.voxels, "out"), _stream(stream)),
            "cubic_rl_deconvolve")
+
+
+def _host_ptr(a, numel, name):
+    import numpy as np
+    if isinstance(a, int):
+        return a
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous() or a.numel() != numel:
+                raise ValueError(f"{name} must be a contiguous float32 host tensor of {numel} elements")
+            return a.data_ptr()
+    except ImportError:
+        pass
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags.c_contiguous or a.size != numel:
+        raise ValueError(f"{name} must be a contiguous float32 host array of {numel} elements")
+    return a.ctypes.data
+
+
+def cubic_rl_deconvolve_host(plan: Plan, image, n_iter: int, eps: float, out, stream=None) -> None:
+    """Host buffers in and out (numpy arrays or CPU tensors; pin them for async copies)."""
+    _check(lib().cubic_rl_deconvolve_host(plan.handle, _host_ptr(image, plan.voxels, "image"), int(n_iter),
+                                          float(eps), _host_ptr(out, plan.voxels, "out"), _stream(stream)),
+           "cubic_rl_deconvolve_host")
+
+
+def cubic_psf_gaussian(dims, sigma_xy: float, sigma_z: float, amp: float, psf, stream=None) -> None:
+    import torch
+    dims = tuple(int(d) for d in dims)
+    d = (_i64 * 3)(*dims)
+    _check(lib().cubic_psf_gaussian(d, float(sigma_xy), float(sigma_z), float(amp),
+                                    _ptr(psf, torch.float32, dims[0] * dims[1] * dims[2], "psf"), _stream(stream)),
+           "cubic_psf_gaussian")
+
+
+def cubic_rl_stream_status(plan: Plan, stream=None) -> None:
+    """Raise CubicError(CUBIC_ERR_TIMEOUT) if a kernel's bounded device wait gave up."""
+    _check(lib().cubic_rl_stream_status(plan.handle, _stream(stream)), "cubic_rl_stream_status")
+
+
+def cubic_rl_plan_variants(plan: Plan):
+    """((nx, ny, nz) variant counts, (vx, vy, vz) chosen)."""
+    c = (_ci * 3)()
+    ch = (_ci * 3)()
+    _check(lib().cubic_rl_plan_variants(plan.handle, c, ch), "cubic_rl_plan_variants")
+    return tuple(c), tuple(ch)
+
+
+def cubic_rl_plan_set_variants(plan: Plan, vx: int, vy: int, vz: int) -> None:
+    _check(lib().cubic_rl_plan_set_variants(plan.handle, int(vx), int(vy), int(vz)), "cubic_rl_plan_set_variants")
+
+
+def cubic_rl_plan_set_chunk(plan: Plan, columns: int) -> None:
+    _check(lib().cubic_rl_plan_set_chunk(plan.handle, int(columns)), "cubic_rl_plan_set_chunk")
+
+
+def cubic_rl_plan_chunk(plan: Plan) -> int:
+    return int(lib().cubic_rl_plan_chunk(plan.handle))
+
+
+def cubic_rl_autotune(plan: Plan, image, out, stream=None) -> None:
+    import torch
+    _check(lib().cubic_rl_autotune(plan.handle, _ptr(image, torch.float32, plan.voxels, "image"),
+                                   _ptr(out, torch.float32, plan.voxels, "out"), _stream(stream)),
+           "cubic_rl_autotune")
+
+
+def cubic_rl_kernel_kinds() -> int:
+    return int(lib().cubic_rl_kernel_kinds())
+
+
+def cubic_rl_kernel_name(kind: int) -> str:
+    return lib().cubic_rl_kernel_name(int(kind)).decode()
+
+
+def cubic_rl_profile(plan: Plan, enable: bool, max_events: int = 1 << 15) -> None:
+    _check(lib().cubic_rl_profile(plan.handle, int(bool(enable)), int(max_events)), "cubic_rl_profile")
+
+
+def cubic_rl_profile_read(plan: Plan) -> dict:
+    """{kernel name: dict(ms, timed, launches, bytes)} since the last cubic_rl_profile()."""
+    n = cubic_rl_kernel_kinds()
+    ms = (ctypes.c_double * n)()
+    timed = (_i64 * n)()
+    launches = (_i64 * n)()
+    nbytes = (ctypes.c_double * n)()
+    _check(lib().cubic_rl_profile_read(plan.handle, n, ms, timed, launches, nbytes), "cubic_rl_profile_read")
+    return {cubic_rl_kernel_name(k): dict(ms=ms[k], timed=int(timed[k]), launches=int(launches[k]),
+                                          bytes=nbytes[k]) for k in range(n)}
 
 
 def cubic_rl_convolve(plan: Plan, x, flipped: bool, out, stream=None) -> None:

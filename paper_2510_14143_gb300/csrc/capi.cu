@@ -8,8 +8,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "../../include/cubic_rl.h"
 #include "registry.cuh"
@@ -65,17 +68,16 @@ void register_shard(AxisKernels *table);
 static AxisKernels g_table[kNumLengths];
 static std::once_flag g_table_once;
 
-static void init_table()
+template <int S>
+static void register_all()
 {
-    register_shard<0>(g_table);
-    register_shard<1>(g_table);
-    register_shard<2>(g_table);
-    register_shard<3>(g_table);
-    register_shard<4>(g_table);
-    register_shard<5>(g_table);
-    register_shard<6>(g_table);
-    register_shard<7>(g_table);
+    if constexpr (S < kShards) {
+        register_shard<S>(g_table);
+        register_all<S + 1>();
+    }
 }
+
+static void init_table() { register_all<0>(); }
 
 const AxisKernels *cubic::find_axis(int64_t n)
 {
@@ -85,13 +87,21 @@ const AxisKernels *cubic::find_axis(int64_t n)
     return nullptr;
 }
 
-int cubic::supported_lengths(const int **out)
-{
-    if (out) *out = kLengths;
-    return kNumLengths;
-}
-
 extern "C" int cubic_rl_supported_length(int64_t n) { return find_axis(n) != nullptr; }
+
+PFN_cuTensorMapEncodeTiled_v12000 cubic::tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }();
+    return fn;
+}
 
 // ------------------------------------------------------------------ small kernels
 
@@ -173,18 +183,40 @@ static unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 32)
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// ------------------------------------------------------------------ kernel kinds
+
+enum KernelKind : int {
+    KK_SUM = 0, KK_FILL, KK_SHIFT, KK_X_FWD, KK_X_INV, KK_X_RATIO, KK_X_UPDATE, KK_X_FINAL,
+    KK_Y_FWD, KK_Y_INV, KK_Z_FWD, KK_Z_INV, KK_Z_CONV, KK_Z_CORR, KK_COUNT
+};
+
+static const char *const kKindNames[KK_COUNT] = {
+    "sum", "fill_initial", "center_to_origin", "x_fwd", "x_inv", "x_ratio", "x_update", "x_final",
+    "y_fwd", "y_inv", "z_fwd", "z_inv", "z_conv", "z_corr"};
+
 // ------------------------------------------------------------------ plan
 
 struct cubic_rl_plan_s {
     int device = 0;
     int64_t nz = 0, ny = 0, nx = 0, V = 0, rows = 0, xh = 0, xp = 0;
     const AxisKernels *kx = nullptr, *ky = nullptr, *kz = nullptr;
+    int vx = 0, vy = 0, vz = 0; // launch-shape variant of each pass
+    int64_t chunk = 0;          // spectrum columns per Y/Z chunk (0: all at once)
+    unsigned *err = nullptr;    // device error word (bounded waits), owned
     float2 *H = nullptr;        // [nz][ny][xp], owned
     float2 *tw = nullptr;       // twiddles: x | y | z, owned
     float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
     double *partial = nullptr;  // kReduceBlocks + 1 doubles, owned
     float2 *ws = nullptr;       // spectrum work array
     bool own_ws = false;
+    float *stage_in = nullptr, *stage_out = nullptr;  // device copies for host-buffer calls, owned
+    // launch accounting and optional per-kernel CUDA-event timing
+    int64_t launches[KK_COUNT] = {};
+    double bytes[KK_COUNT] = {};
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;       // pairs (begin, end)
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
 };
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
@@ -201,34 +233,117 @@ static cubic_status_t ensure_workspace(cubic_rl_plan_s *p)
     return CUBIC_OK;
 }
 
+// Algorithmic HBM bytes of one launch of each pass kind: every array the pass
+// must read or write, once (complex half spectrum = rows * xh * 8 bytes).
+static double kind_bytes(const cubic_rl_plan_s *p, int kind)
+{
+    const double spec = (double)p->rows * p->xh * 8.0, real = (double)p->V * 4.0;
+    switch (kind) {
+    case KK_SUM: return real;
+    case KK_FILL: return real;
+    case KK_SHIFT: return 2 * real;
+    case KK_X_FWD: return real + spec;
+    case KK_X_INV: return spec + real;
+    case KK_X_RATIO: return spec + real + spec;
+    case KK_X_UPDATE: return spec + 2 * real + spec;
+    case KK_X_FINAL: return spec + 2 * real;
+    case KK_Y_FWD: case KK_Y_INV: case KK_Z_FWD: case KK_Z_INV: return 2 * spec;
+    case KK_Z_CONV: case KK_Z_CORR: return 3 * spec;
+    }
+    return 0.0;
+}
+
+static void prof_mark(cubic_rl_plan_s *p, int kind, cudaStream_t st)
+{
+    if (!p->prof || p->ev_used >= p->ev.size()) return;
+    if (cudaEventRecord(p->ev[p->ev_used], st) == cudaSuccess) {
+        p->ev_kind[p->ev_used] = kind;
+        ++p->ev_used;
+    }
+}
+
+// Run one launch of `kind`, counting it and (when profiling) bracketing it by events.
+template <class F>
+static cudaError_t counted(cubic_rl_plan_s *p, int kind, cudaStream_t st, F &&launch, double bytes = -1.0)
+{
+    const bool pair = p->prof && p->ev_used + 2 <= p->ev.size();
+    if (pair) prof_mark(p, kind, st);
+    cudaError_t e = launch();
+    if (pair) prof_mark(p, kind, st);
+    p->launches[kind] += 1;
+    p->bytes[kind] += bytes >= 0.0 ? bytes : kind_bytes(p, kind);
+    return e;
+}
+
+static const int kXKind[XM_COUNT] = {KK_X_FWD, KK_X_INV, KK_X_RATIO, KK_X_UPDATE, KK_X_FINAL};
+
+static cudaError_t run_x(cubic_rl_plan_s *p, int mode, const XArgs &a, cudaStream_t st)
+{
+    return counted(p, kXKind[mode], st, [&] { return p->kx->xv[p->vx].fn[mode](a, st); });
+}
+
+static cudaError_t run_y(cubic_rl_plan_s *p, const YArgs &a, cudaStream_t st)
+{
+    const double bytes = 2.0 * 8.0 * (double)p->rows * (double)(a.col1 - a.col0);
+    return counted(p, a.inverse ? KK_Y_INV : KK_Y_FWD, st, [&] { return p->ky->yzv[p->vy].y(a, st); }, bytes);
+}
+
+static cudaError_t run_z(cubic_rl_plan_s *p, const ZArgs &a, cudaStream_t st)
+{
+    static const int kind[4] = {KK_Z_FWD, KK_Z_CONV, KK_Z_CORR, KK_Z_INV};
+    const double arrays = (a.mode == ZM_CONV || a.mode == ZM_CORR) ? 3.0 : 2.0;
+    const double bytes = arrays * 8.0 * (double)p->rows * (double)(a.col1 - a.col0);
+    return counted(p, kind[a.mode], st, [&] { return p->kz->yzv[p->vz].z(a, st); }, bytes);
+}
+
+static YArgs y_args(const cubic_rl_plan_s *p, float2 *spec, int inverse, int64_t c0, int64_t c1)
+{
+    return YArgs{spec, p->tw_y, p->nz, p->xh, p->xp, inverse, c0, c1, p->err};
+}
+
+static ZArgs z_args(const cubic_rl_plan_s *p, float2 *spec, int mode, float scale, int64_t c0, int64_t c1)
+{
+    return ZArgs{spec, p->H, p->tw_z, p->ny, p->xh, p->xp, mode, scale, c0, c1, p->err, p->nz};
+}
+
+static XArgs x_args(const cubic_rl_plan_s *p)
+{
+    XArgs a{};
+    a.tw = p->tw_x;
+    a.rows = p->rows;
+    a.xp = p->xp;
+    a.err = p->err;
+    return a;
+}
+
 // Forward 3D real-to-half-complex transform of `real` into `spec`, optionally
 // scaled (scale applies in the Z pass).
 static cubic_status_t enqueue_forward3(cubic_rl_plan_s *p, const float *real, float2 *spec, float scale,
                                        cudaStream_t st)
 {
-    XArgs xa{};
+    XArgs xa = x_args(p);
     xa.spec_out = spec;
     xa.src = real;
-    xa.tw = p->tw_x;
-    xa.rows = p->rows;
-    xa.xp = p->xp;
-    CUBIC_CUDA(p->kx->x[XM_FWD](xa, st));
-    YArgs ya{spec, p->tw_y, p->nz, p->xh, p->xp, 0};
-    CUBIC_CUDA(p->ky->y(ya, st));
-    ZArgs za{spec, nullptr, p->tw_z, p->ny, p->xh, p->xp, ZM_FWD_SCALE, scale};
-    CUBIC_CUDA(p->kz->z(za, st));
+    CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
+    CUBIC_CUDA(run_y(p, y_args(p, spec, 0, 0, p->xh), st));
+    CUBIC_CUDA(run_z(p, z_args(p, spec, ZM_FWD_SCALE, scale, 0, p->xh), st));
     return CUBIC_OK;
 }
 
 // Y forward, Z (product with H or conj H), Y inverse on the plan's spectrum.
+// With p->chunk > 0 the three passes run chunk by chunk over groups of
+// p->chunk spectrum columns, so that a chunk written by one pass is still in
+// L2 when the next pass reads it: per voxel, HBM then sees one read and one
+// write of the spectrum (plus H) instead of three of each.
 static cubic_status_t enqueue_yzy(cubic_rl_plan_s *p, float2 *spec, int zmode, cudaStream_t st)
 {
-    YArgs ya{spec, p->tw_y, p->nz, p->xh, p->xp, 0};
-    CUBIC_CUDA(p->ky->y(ya, st));
-    ZArgs za{spec, p->H, p->tw_z, p->ny, p->xh, p->xp, zmode, 1.f};
-    CUBIC_CUDA(p->kz->z(za, st));
-    ya.inverse = 1;
-    CUBIC_CUDA(p->ky->y(ya, st));
+    const int64_t step = p->chunk > 0 ? p->chunk : p->xh;
+    for (int64_t c0 = 0; c0 < p->xh; c0 += step) {
+        const int64_t c1 = c0 + step < p->xh ? c0 + step : p->xh;
+        CUBIC_CUDA(run_y(p, y_args(p, spec, 0, c0, c1), st));
+        CUBIC_CUDA(run_z(p, z_args(p, spec, zmode, 1.f, c0, c1), st));
+        CUBIC_CUDA(run_y(p, y_args(p, spec, 1, c0, c1), st));
+    }
     return CUBIC_OK;
 }
 
@@ -238,9 +353,69 @@ static cubic_status_t load_psf(cubic_rl_plan_s *p, const float *psf, cudaStream_
     if (s != CUBIC_OK) return s;
     // the shifted real PSF fits in the workspace (xp >= nx/2+1 complex >= nx floats)
     float *h0 = (float *)p->ws;
-    k_center_to_origin<<<grid_for(p->V, 256), 256, 0, st>>>(psf, h0, p->nz, p->ny, p->nx);
-    CUBIC_CUDA(cudaGetLastError());
+    CUBIC_CUDA(counted(p, KK_SHIFT, st, [&] {
+        k_center_to_origin<<<grid_for(p->V, 256), 256, 0, st>>>(psf, h0, p->nz, p->ny, p->nx);
+        return cudaGetLastError();
+    }));
     return enqueue_forward3(p, h0, p->H, (float)(1.0 / (double)p->V), st);
+}
+
+// ------------------------------------------------------------------ tuning cache
+// Chosen variants per volume shape, shared by every plan of this process and,
+// when CUBIC_TUNE_CACHE names a file, persisted there as lines "nz ny nx vx vy vz".
+
+struct TuneEntry {
+    int64_t nz, ny, nx;
+    int vx, vy, vz;
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tune;
+static bool g_tune_loaded = false;
+
+static void tune_load_locked()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("CUBIC_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    TuneEntry e;
+    long long a, b, c;
+    while (fscanf(f, "%lld %lld %lld %d %d %d", &a, &b, &c, &e.vx, &e.vy, &e.vz) == 6) {
+        e.nz = a;
+        e.ny = b;
+        e.nx = c;
+        g_tune.push_back(e);
+    }
+    fclose(f);
+}
+
+static void tuned_variants(cubic_rl_plan_s *p)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    for (const TuneEntry &e : g_tune)
+        if (e.nz == p->nz && e.ny == p->ny && e.nx == p->nx && e.vx < p->kx->nx && e.vy < p->ky->nyz &&
+            e.vz < p->kz->nyz) {
+            p->vx = e.vx;
+            p->vy = e.vy;
+            p->vz = e.vz;
+        }
+}
+
+static void tune_store(const cubic_rl_plan_s *p)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    g_tune.push_back({p->nz, p->ny, p->nx, p->vx, p->vy, p->vz});
+    const char *path = getenv("CUBIC_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%lld %lld %lld %d %d %d\n", (long long)p->nz, (long long)p->ny, (long long)p->nx, p->vx, p->vy,
+            p->vz);
+    fclose(f);
 }
 
 extern "C" cubic_status_t cubic_rl_plan(cubic_rl_plan_t *plan, const int64_t dims[3], const float *psf,
@@ -291,6 +466,12 @@ extern "C" cubic_status_t cubic_rl_plan(cubic_rl_plan_t *plan, const int64_t dim
     e = cudaMalloc(&mem, (kReduceBlocks + 1) * sizeof(double));
     if (e != cudaSuccess) return bail(fail(CUBIC_ERR_OUT_OF_MEMORY, "reduction: %s", cudaGetErrorString(e)));
     p->partial = (double *)mem;
+    e = cudaMalloc(&mem, sizeof(unsigned));
+    if (e != cudaSuccess) return bail(fail(CUBIC_ERR_OUT_OF_MEMORY, "error word: %s", cudaGetErrorString(e)));
+    p->err = (unsigned *)mem;
+    e = cudaMemsetAsync(p->err, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return bail(fail(CUBIC_ERR_CUDA, "error word: %s", cudaGetErrorString(e)));
+    tuned_variants(p);
 
     k_twiddles<<<grid_for(p->nx, 128, 1 << 20), 128, 0, st>>>(p->tw_x, (int)p->nx);
     k_twiddles<<<grid_for(p->ny, 128, 1 << 20), 128, 0, st>>>(p->tw_y, (int)p->ny);
@@ -317,7 +498,11 @@ extern "C" cubic_status_t cubic_rl_plan_destroy(cubic_rl_plan_t plan)
     cudaFree(plan->H);
     cudaFree(plan->tw);
     cudaFree(plan->partial);
+    cudaFree(plan->err);
     if (plan->own_ws) cudaFree(plan->ws);
+    cudaFree(plan->stage_in);
+    cudaFree(plan->stage_out);
+    for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
     delete plan;
     return CUBIC_OK;
 }
@@ -355,30 +540,33 @@ static cubic_status_t enqueue_rl(cubic_rl_plan_s *p, const float *image, int n_i
                                  float2 *spec, cudaStream_t st)
 {
     // u0 = max(mean(image), eps)
-    k_sum_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(image, p->V, p->partial);
-    k_sum_final<<<1, kReduceThreads, 0, st>>>(p->partial, kReduceBlocks, p->partial + kReduceBlocks);
-    k_fill_initial<<<grid_for(p->V, 256), 256, 0, st>>>(out, p->V, p->partial + kReduceBlocks, eps);
-    CUBIC_CUDA(cudaGetLastError());
+    CUBIC_CUDA(counted(p, KK_SUM, st, [&] {
+        k_sum_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(image, p->V, p->partial);
+        k_sum_final<<<1, kReduceThreads, 0, st>>>(p->partial, kReduceBlocks, p->partial + kReduceBlocks);
+        return cudaGetLastError();
+    }));
+    p->launches[KK_SUM] += 1;  // two kernels
+    CUBIC_CUDA(counted(p, KK_FILL, st, [&] {
+        k_fill_initial<<<grid_for(p->V, 256), 256, 0, st>>>(out, p->V, p->partial + kReduceBlocks, eps);
+        return cudaGetLastError();
+    }));
     if (n_iter == 0) return CUBIC_OK;
 
-    XArgs xa{};
+    XArgs xa = x_args(p);
     xa.spec_in = spec;
     xa.spec_out = spec;
     xa.src = out;
     xa.u = out;
     xa.dst = out;
     xa.d = image;
-    xa.tw = p->tw_x;
-    xa.rows = p->rows;
-    xa.xp = p->xp;
     xa.eps = eps;
-    CUBIC_CUDA(p->kx->x[XM_FWD](xa, st));  // spectrum of u0
+    CUBIC_CUDA(run_x(p, XM_FWD, xa, st));  // spectrum of u0
     cubic_status_t s;
     for (int k = 0; k < n_iter; ++k) {
         if ((s = enqueue_yzy(p, spec, ZM_CONV, st)) != CUBIC_OK) return s;   // b = h * u
-        CUBIC_CUDA(p->kx->x[XM_RATIO](xa, st));                              // r = d / max(b, eps)
+        CUBIC_CUDA(run_x(p, XM_RATIO, xa, st));                              // r = d / max(b, eps)
         if ((s = enqueue_yzy(p, spec, ZM_CORR, st)) != CUBIC_OK) return s;   // q = h (flipped) * r
-        CUBIC_CUDA(p->kx->x[k + 1 < n_iter ? XM_UPDATE : XM_FINAL](xa, st)); // u = u * q
+        CUBIC_CUDA(run_x(p, k + 1 < n_iter ? XM_UPDATE : XM_FINAL, xa, st)); // u = u * q
     }
     return CUBIC_OK;
 }
@@ -407,17 +595,14 @@ extern "C" cubic_status_t cubic_rl_convolve(cubic_rl_plan_t plan, const float *i
     cubic_status_t s = ensure_workspace(plan);
     if (s != CUBIC_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    XArgs xa{};
+    XArgs xa = x_args(plan);
     xa.spec_in = plan->ws;
     xa.spec_out = plan->ws;
     xa.src = in;
     xa.dst = out;
-    xa.tw = plan->tw_x;
-    xa.rows = plan->rows;
-    xa.xp = plan->xp;
-    CUBIC_CUDA(plan->kx->x[XM_FWD](xa, st));
+    CUBIC_CUDA(run_x(plan, XM_FWD, xa, st));
     if ((s = enqueue_yzy(plan, plan->ws, flipped ? ZM_CORR : ZM_CONV, st)) != CUBIC_OK) return s;
-    CUBIC_CUDA(plan->kx->x[XM_INV](xa, st));
+    CUBIC_CUDA(run_x(plan, XM_INV, xa, st));
     return CUBIC_OK;
 }
 
@@ -442,16 +627,315 @@ extern "C" cubic_status_t cubic_rl_fft3_inverse(cubic_rl_plan_t plan, void *spec
     if (!aligned16(out) || !aligned16(spec)) return fail(CUBIC_ERR_ALIGNMENT, "out and spec must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     float2 *sp = (float2 *)spec;
-    ZArgs za{sp, nullptr, plan->tw_z, plan->ny, plan->xh, plan->xp, ZM_INV_SCALE, (float)(1.0 / (double)plan->V)};
-    CUBIC_CUDA(plan->kz->z(za, st));
-    YArgs ya{sp, plan->tw_y, plan->nz, plan->xh, plan->xp, 1};
-    CUBIC_CUDA(plan->ky->y(ya, st));
-    XArgs xa{};
+    CUBIC_CUDA(run_z(plan, z_args(plan, sp, ZM_INV_SCALE, (float)(1.0 / (double)plan->V), 0, plan->xh), st));
+    CUBIC_CUDA(run_y(plan, y_args(plan, sp, 1, 0, plan->xh), st));
+    XArgs xa = x_args(plan);
     xa.spec_in = sp;
     xa.dst = out;
-    xa.tw = plan->tw_x;
-    xa.rows = plan->rows;
-    xa.xp = plan->xp;
-    CUBIC_CUDA(plan->kx->x[XM_INV](xa, st));
+    CUBIC_CUDA(run_x(plan, XM_INV, xa, st));
+    return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ host buffers
+
+extern "C" cubic_status_t cubic_rl_deconvolve_host(cubic_rl_plan_t plan, const float *image, int n_iter, float eps,
+                                                   float *out, void *stream)
+{
+    if (!plan || !image || !out) return fail(CUBIC_ERR_INVALID_ARG, "plan, image and out must be non-null");
+    if (n_iter < 0) return fail(CUBIC_ERR_INVALID_ARG, "n_iter must be >= 0");
+    if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
+    const size_t nbytes = (size_t)plan->V * sizeof(float);
+    if (overlaps(image, out, nbytes)) return fail(CUBIC_ERR_INVALID_ARG, "out must not overlap image");
+    cubic_status_t s = ensure_workspace(plan);
+    if (s != CUBIC_OK) return s;
+    if (!plan->stage_in) {
+        void *a = nullptr, *b = nullptr;
+        CUBIC_CUDA(cudaMalloc(&a, nbytes));
+        cudaError_t e = cudaMalloc(&b, nbytes);
+        if (e != cudaSuccess) {
+            cudaFree(a);
+            return fail(CUBIC_ERR_OUT_OF_MEMORY, "staging: %s", cudaGetErrorString(e));
+        }
+        plan->stage_in = (float *)a;
+        plan->stage_out = (float *)b;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CUBIC_CUDA(cudaMemcpyAsync(plan->stage_in, image, nbytes, cudaMemcpyHostToDevice, st));
+    s = enqueue_rl(plan, plan->stage_in, n_iter, eps, plan->stage_out, plan->ws, st);
+    if (s != CUBIC_OK) return s;
+    CUBIC_CUDA(cudaMemcpyAsync(out, plan->stage_out, nbytes, cudaMemcpyDeviceToHost, st));
+    return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ profiling
+
+extern "C" int cubic_rl_kernel_kinds(void) { return KK_COUNT; }
+
+extern "C" const char *cubic_rl_kernel_name(int kind)
+{
+    return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "";
+}
+
+extern "C" cubic_status_t cubic_rl_profile(cubic_rl_plan_t plan, int enable, int max_events)
+{
+    if (!plan) return fail(CUBIC_ERR_INVALID_ARG, "plan must be non-null");
+    for (int k = 0; k < KK_COUNT; ++k) {
+        plan->launches[k] = 0;
+        plan->bytes[k] = 0.0;
+    }
+    plan->ev_used = 0;
+    plan->prof = enable != 0;
+    if (enable) {
+        if (max_events < 2) max_events = 2;
+        while ((int)plan->ev.size() < max_events) {
+            cudaEvent_t e;
+            CUBIC_CUDA(cudaEventCreate(&e));
+            plan->ev.push_back(e);
+        }
+        plan->ev_kind.assign(plan->ev.size(), 0);
+    }
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_rl_profile_read(cubic_rl_plan_t plan, int n_kinds, double *total_ms,
+                                                int64_t *timed_launches, int64_t *launches, double *bytes)
+{
+    if (!plan || n_kinds < 0) return fail(CUBIC_ERR_INVALID_ARG, "bad arguments");
+    const int nk = n_kinds < KK_COUNT ? n_kinds : KK_COUNT;
+    for (int k = 0; k < nk; ++k) {
+        if (total_ms) total_ms[k] = 0.0;
+        if (timed_launches) timed_launches[k] = 0;
+        if (launches) launches[k] = plan->launches[k];
+        if (bytes) bytes[k] = plan->bytes[k];
+    }
+    if (plan->ev_used >= 2) CUBIC_CUDA(cudaEventSynchronize(plan->ev[plan->ev_used - 1]));
+    for (size_t i = 0; i + 1 < plan->ev_used; i += 2) {
+        float ms = 0.f;
+        CUBIC_CUDA(cudaEventElapsedTime(&ms, plan->ev[i], plan->ev[i + 1]));
+        const int k = plan->ev_kind[i];
+        if (k < nk) {
+            if (total_ms) total_ms[k] += ms;
+            if (timed_launches) timed_launches[k] += 1;
+        }
+    }
+    return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ Gaussian PSF
+
+// g = exp(-(dx^2+dy^2) a_xy - dz^2 a_z), (dx,dy,dz) = index - floor(n/2); block partial
+// sums of g in double (the PSF's flux) for the normalisation.
+__global__ void __launch_bounds__(kReduceThreads) k_psf_gauss(float *__restrict__ psf, int64_t nz, int64_t ny,
+                                                              int64_t nx, float a_xy, float a_z,
+                                                              double *__restrict__ partial)
+{
+    __shared__ double sh[kReduceThreads / 32];
+    const int64_t V = nz * ny * nx;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        const float dx = (float)(i % nx - nx / 2);
+        const float dy = (float)((i / nx) % ny - ny / 2);
+        const float dz = (float)(i / (nx * ny) - nz / 2);
+        const float g = expf(-(dx * dx + dy * dy) * a_xy - dz * dz * a_z);
+        psf[i] = g;
+        s += (double)g;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < kReduceThreads / 32 ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_scale_by_sum(float *__restrict__ x, int64_t n, const double *__restrict__ sum, double amp)
+{
+    const float f = (float)(amp / sum[0]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] *= f;
+}
+
+extern "C" cubic_status_t cubic_psf_gaussian(const int64_t dims[3], float sigma_xy, float sigma_z, float amp,
+                                             float *psf, void *stream)
+{
+    if (!dims || !psf) return fail(CUBIC_ERR_INVALID_ARG, "dims and psf must be non-null");
+    for (int i = 0; i < 3; ++i)
+        if (dims[i] < 1) return fail(CUBIC_ERR_INVALID_ARG, "dims must be >= 1");
+    if (!(sigma_xy > 0.f) || !(sigma_z > 0.f) || !(sigma_xy < INFINITY) || !(sigma_z < INFINITY) ||
+        !(fabsf(amp) < INFINITY))
+        return fail(CUBIC_ERR_INVALID_ARG, "sigmas must be finite and > 0, amp finite");
+    if (!aligned16(psf)) return fail(CUBIC_ERR_ALIGNMENT, "psf must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t V = dims[0] * dims[1] * dims[2];
+    void *scratch = nullptr;
+    CUBIC_CUDA(cudaMallocAsync(&scratch, (kReduceBlocks + 1) * sizeof(double), st));
+    double *partial = (double *)scratch;
+    const float a_xy = (float)(0.5 / ((double)sigma_xy * sigma_xy));
+    const float a_z = (float)(0.5 / ((double)sigma_z * sigma_z));
+    k_psf_gauss<<<kReduceBlocks, kReduceThreads, 0, st>>>(psf, dims[0], dims[1], dims[2], a_xy, a_z, partial);
+    k_sum_final<<<1, kReduceThreads, 0, st>>>(partial, kReduceBlocks, partial + kReduceBlocks);
+    k_scale_by_sum<<<grid_for(V, 256), 256, 0, st>>>(psf, V, partial + kReduceBlocks, (double)amp);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return fail(CUBIC_ERR_CUDA, "psf kernels: %s", cudaGetErrorString(e));
+    return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ variants and tuning
+
+extern "C" cubic_status_t cubic_rl_plan_variants(cubic_rl_plan_t plan, int counts[3], int chosen[3])
+{
+    if (!plan) return fail(CUBIC_ERR_INVALID_ARG, "plan must be non-null");
+    if (counts) {
+        counts[0] = plan->kx->nx;
+        counts[1] = plan->ky->nyz;
+        counts[2] = plan->kz->nyz;
+    }
+    if (chosen) {
+        chosen[0] = plan->vx;
+        chosen[1] = plan->vy;
+        chosen[2] = plan->vz;
+    }
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_rl_plan_set_variants(cubic_rl_plan_t plan, int vx, int vy, int vz)
+{
+    if (!plan) return fail(CUBIC_ERR_INVALID_ARG, "plan must be non-null");
+    if (vx < 0 || vx >= plan->kx->nx || vy < 0 || vy >= plan->ky->nyz || vz < 0 || vz >= plan->kz->nyz)
+        return fail(CUBIC_ERR_INVALID_ARG, "variant index out of range");
+    plan->vx = vx;
+    plan->vy = vy;
+    plan->vz = vz;
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_rl_plan_set_chunk(cubic_rl_plan_t plan, int64_t columns)
+{
+    if (!plan) return fail(CUBIC_ERR_INVALID_ARG, "plan must be non-null");
+    if (columns < 0 || columns % 16 != 0) return fail(CUBIC_ERR_INVALID_ARG, "chunk must be a multiple of 16 (0: off)");
+    plan->chunk = columns;
+    return CUBIC_OK;
+}
+
+extern "C" int64_t cubic_rl_plan_chunk(cubic_rl_plan_t plan) { return plan ? plan->chunk : -1; }
+
+// Best-of-3 device time of `body` (after one untimed run); `prepare` runs,
+// untimed, before every run.
+template <class G, class F>
+static cubic_status_t time_best(cudaStream_t st, G &&prepare, F &&body, float *best_ms)
+{
+    cudaEvent_t e0, e1;
+    CUBIC_CUDA(cudaEventCreate(&e0));
+    CUBIC_CUDA(cudaEventCreate(&e1));
+    cubic_status_t s = prepare();
+    if (s == CUBIC_OK) s = body();
+    float best = 1e30f;
+    for (int r = 0; r < 3 && s == CUBIC_OK; ++r) {
+        s = prepare();
+        if (s != CUBIC_OK) break;
+        cudaEventRecord(e0, st);
+        s = body();
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) s = fail(CUBIC_ERR_CUDA, "tuning sync failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *best_ms = best;
+    return s;
+}
+
+extern "C" cubic_status_t cubic_rl_autotune(cubic_rl_plan_t plan, const float *image, float *out, void *stream)
+{
+    if (!plan || !image || !out) return fail(CUBIC_ERR_INVALID_ARG, "plan, image and out must be non-null");
+    if (!aligned16(image) || !aligned16(out)) return fail(CUBIC_ERR_ALIGNMENT, "image and out must be 16-byte aligned");
+    if (overlaps(image, out, (size_t)plan->V * sizeof(float)))
+        return fail(CUBIC_ERR_INVALID_ARG, "out must not overlap image");
+    cubic_status_t s = ensure_workspace(plan);
+    if (s != CUBIC_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool prof = plan->prof;
+    plan->prof = false;
+    float2 *ws = plan->ws;
+    // every timed run starts from the spectrum of the image and a copy of it as estimate
+    auto prepare = [&]() -> cubic_status_t {
+        CUBIC_CUDA(cudaMemcpyAsync(out, image, (size_t)plan->V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        return enqueue_forward3(plan, image, ws, 1.f / (float)plan->V, st);
+    };
+    auto nothing = []() -> cubic_status_t { return CUBIC_OK; };
+    float best, ms;
+    // X pass: one ratio and one update launch
+    int bx = plan->vx;
+    best = 1e30f;
+    for (int v = 0; v < plan->kx->nx && s == CUBIC_OK; ++v) {
+        plan->vx = v;
+        XArgs xa = x_args(plan);
+        xa.spec_in = ws;
+        xa.spec_out = ws;
+        xa.u = out;
+        xa.d = image;
+        xa.eps = 1.f;
+        s = time_best(st, prepare, [&]() -> cubic_status_t {
+            CUBIC_CUDA(run_x(plan, XM_RATIO, xa, st));
+            CUBIC_CUDA(run_x(plan, XM_UPDATE, xa, st));
+            return CUBIC_OK;
+        }, &ms);
+        if (ms < best) { best = ms; bx = v; }
+    }
+    plan->vx = bx;
+    // Y pass: forward + inverse
+    int by = plan->vy;
+    best = 1e30f;
+    for (int v = 0; v < plan->ky->nyz && s == CUBIC_OK; ++v) {
+        plan->vy = v;
+        YArgs ya = y_args(plan, ws, 0, 0, plan->xh);
+        s = time_best(st, nothing, [&]() -> cubic_status_t {
+            ya.inverse = 0;
+            CUBIC_CUDA(run_y(plan, ya, st));
+            ya.inverse = 1;
+            CUBIC_CUDA(run_y(plan, ya, st));
+            return CUBIC_OK;
+        }, &ms);
+        if (ms < best) { best = ms; by = v; }
+    }
+    plan->vy = by;
+    // Z pass: spectral product with H
+    int bz = plan->vz;
+    best = 1e30f;
+    for (int v = 0; v < plan->kz->nyz && s == CUBIC_OK; ++v) {
+        plan->vz = v;
+        ZArgs za = z_args(plan, ws, ZM_CONV, 1.f, 0, plan->xh);
+        s = time_best(st, nothing, [&]() -> cubic_status_t {
+            CUBIC_CUDA(run_z(plan, za, st));
+            return CUBIC_OK;
+        }, &ms);
+        if (ms < best) { best = ms; bz = v; }
+    }
+    plan->vz = bz;
+    plan->prof = prof;
+    if (s == CUBIC_OK) s = prepare();  // leave finite data behind
+    if (s != CUBIC_OK) return s;
+    tune_store(plan);
+    return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ device status
+
+extern "C" cubic_status_t cubic_rl_stream_status(cubic_rl_plan_t plan, void *stream)
+{
+    if (!plan) return fail(CUBIC_ERR_INVALID_ARG, "plan must be non-null");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned word = 0;
+    CUBIC_CUDA(cudaMemcpyAsync(&word, plan->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CUBIC_CUDA(cudaStreamSynchronize(st));
+    if (word) {
+        CUBIC_CUDA(cudaMemsetAsync(plan->err, 0, sizeof(unsigned), st));
+        return fail(CUBIC_ERR_TIMEOUT, "a device wait timed out (error word 0x%x)", word);
+    }
     return CUBIC_OK;
 }

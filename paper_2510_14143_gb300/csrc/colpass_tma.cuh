@@ -1,0 +1,217 @@
+// colpass_tma.cuh -- persistent, TMA-pipelined Y and Z passes.
+//
+// A tile is B adjacent spectrum columns x one full line (N elements) along y
+// (Y pass, lines at stride xp) or along z (Z pass, lines at stride ny*xp).  A
+// persistent CTA walks its tiles with two shared-memory stages: while tile i
+// is being transformed, the TMA engine loads tile i+1 into the other stage and
+// stores tile i-1 back to HBM.  Tiles move as 3D tensor boxes over the
+// spectrum viewed as float32 [nz][ny][2*xp] (box {2B, rows, 1} for Y,
+// {2B, 1, rows} for Z), so they land in shared memory as [line position][column],
+// which is also the layout the line FFT exchanges through.
+//
+// The Z pass multiplies by H (forward convolution) or conj(H) (correlation
+// with the PSF, i.e. convolution with the flipped PSF) between its forward and
+// inverse transforms; the H tile rides on the same mbarrier as the data tile.
+#pragma once
+
+#include <cuda.h>
+
+#include "passes.cuh"
+
+namespace cubic {
+
+enum ColKind : int { COL_Y = 0, COL_Z = 1 };
+
+struct ColArgs {
+    const float2 *tw;
+    int64_t ntiles_col;  // column tiles per plane / row
+    int64_t ntiles;      // total tiles
+    int64_t col_tile0;   // first column tile of this launch
+    int mode;            // Y: 0 forward, 1 inverse.  Z: a ZMode
+    float scale;         // ZM_FWD_SCALE / ZM_INV_SCALE
+    unsigned *err;
+};
+
+// largest divisor of n that is <= 256 (TMA box extent limit)
+constexpr int box_rows(int n)
+{
+    for (int d = n < 256 ? n : 256; d > 1; --d)
+        if (n % d == 0) return d;
+    return 1;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *smem_dst, const CUtensorMap *tm, int c0, int c1, int c2,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(smem_dst)),
+        "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, int c0, int c1, int c2, const void *smem_src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tm),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(smem_src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <int S>
+struct SmemStridedT {  // element pos at base[pos * S]
+    float2 *base;
+    __device__ __forceinline__ float2 &at(int pos) const { return base[pos * S]; }
+};
+
+// one stage holds a tile; rounded up to 1 KB so that every stage (and every
+// box inside it, whose offsets are multiples of R*B*8 bytes) starts on the
+// alignment tensor copies need
+template <int N, int B>
+constexpr size_t col_stage_bytes()
+{
+    return ((size_t)N * B * sizeof(float2) + 1023) / 1024 * 1024;
+}
+
+template <int N, int B>
+constexpr size_t col_tile_bytes()
+{
+    return (size_t)N * B * sizeof(float2);
+}
+
+template <int N, int B, int KIND>
+constexpr size_t col_smem_bytes()
+{
+    // 1 KB for the barriers (keeps the stages 1 KB aligned), two data stages,
+    // two H stages for the Z pass
+    return 1024 + 2 * col_stage_bytes<N, B>() * (KIND == COL_Z ? 2 : 1);
+}
+
+template <int N, int P, int B, int KIND>
+__global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CUtensorMap tm_spec,
+                                                      const __grid_constant__ CUtensorMap tm_h, ColArgs a)
+{
+    constexpr int E = N / P;
+    constexpr int R = box_rows(N);
+    constexpr int NB = N / R;  // boxes per tile
+    constexpr size_t SB = col_stage_bytes<N, B>();
+    extern __shared__ __align__(1024) unsigned char smem_col[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_col);  // full[0], full[1]
+    float2 *stage[2] = {reinterpret_cast<float2 *>(smem_col + 1024),
+                        reinterpret_cast<float2 *>(smem_col + 1024 + SB)};
+    float2 *hstage[2] = {reinterpret_cast<float2 *>(smem_col + 1024 + 2 * SB),
+                         reinterpret_cast<float2 *>(smem_col + 1024 + 3 * SB)};
+    const bool needH = (KIND == COL_Z) && (a.mode == ZM_CONV || a.mode == ZM_CORR);
+    const unsigned tile_bytes = (unsigned)(col_tile_bytes<N, B>() * (needH ? 2 : 1));
+
+    const int b = threadIdx.x % B;
+    const int t = threadIdx.x / B;
+    auto sync = [] { __syncthreads(); };
+    using FFT = LineFFT<N, P>;
+
+    // tile -> tensor coordinates of its first box
+    auto coords = [&](int64_t tile, int &cx, int &o) {
+        const int64_t ct = a.col_tile0 + tile % a.ntiles_col;
+        o = (int)(tile / a.ntiles_col);  // z for Y, y for Z
+        cx = (int)(ct * B * 2);
+    };
+    auto issue = [&](int64_t tile, int s) {
+        int cx, o;
+        coords(tile, cx, o);
+        mbar_arrive_expect_tx(&full[s], tile_bytes);
+        for (int j = 0; j < NB; ++j) {
+            float2 *dst = stage[s] + (size_t)j * R * B;
+            if (KIND == COL_Y)
+                tma_load_3d(dst, &tm_spec, cx, j * R, o, &full[s]);
+            else
+                tma_load_3d(dst, &tm_spec, cx, o, j * R, &full[s]);
+            if (needH) tma_load_3d(hstage[s] + (size_t)j * R * B, &tm_h, cx, o, j * R, &full[s]);
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int64_t tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < a.ntiles) issue(tile, 0);
+
+    for (int it = 0; tile < a.ntiles; tile += gridDim.x, ++it) {
+        const int s = it & 1;
+        const unsigned phase = (unsigned)((it >> 1) & 1);
+        const int64_t next = tile + gridDim.x;
+        if (threadIdx.x == 0 && next < a.ntiles) {
+            bulk_wait_read_all();  // the other stage's store has left shared memory
+            issue(next, s ^ 1);
+        }
+        const bool arrived = mbar_wait_bounded(&full[s], phase, a.err);
+        if (!__syncthreads_and(arrived)) {
+            // give an already issued load of the next tile a bounded chance to land
+            if (threadIdx.x == 0 && next < a.ntiles)
+                mbar_wait_bounded(&full[s ^ 1], (unsigned)(((it + 1) >> 1) & 1), a.err);
+            break;
+        }
+
+        float2 *buf = stage[s];
+        SmemStridedT<B> sm{buf + b};
+        float2 v[E];
+        const bool conj_in = (KIND == COL_Y) ? a.mode == 1 : a.mode == ZM_INV_SCALE;
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            const float2 x = buf[(t + P * i) * B + b];
+            v[i] = conj_in ? cconj(x) : x;
+        });
+        __syncthreads();  // every canonical read is done before the exchanges reuse the stage
+        FFT::forward(v, sm, a.tw, t, sync);
+        if (KIND == COL_Z && needH) {
+            const float2 *hb = hstage[s];
+            const bool corr = a.mode == ZM_CORR;
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                const float2 h = hb[(t + P * i) * B + b];
+                v[i] = cconj(corr ? cmulconj(v[i], h) : cmul(v[i], h));
+            });
+            FFT::forward(v, sm, a.tw, t, sync);
+            static_for<0, E>([&](auto i_) { v[CUBIC_CI(i_)] = cconj(v[CUBIC_CI(i_)]); });
+        } else if (KIND == COL_Z) {
+            const float sc = a.scale, sy = conj_in ? -a.scale : a.scale;
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                v[i] = make_float2(v[i].x * sc, v[i].y * sy);
+            });
+        } else if (conj_in) {
+            static_for<0, E>([&](auto i_) { v[CUBIC_CI(i_)] = cconj(v[CUBIC_CI(i_)]); });
+        }
+        // canonical positions are owned by this thread: no barrier needed before writing
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            buf[(t + P * i) * B + b] = v[i];
+        });
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int cx, o;
+            coords(tile, cx, o);
+            for (int j = 0; j < NB; ++j) {
+                const float2 *src = buf + (size_t)j * R * B;
+                if (KIND == COL_Y)
+                    tma_store_3d(&tm_spec, cx, j * R, o, src);
+                else
+                    tma_store_3d(&tm_spec, cx, o, j * R, src);
+            }
+            bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
+}
+
+}  // namespace cubic

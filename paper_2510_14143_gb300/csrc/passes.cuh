@@ -21,6 +21,7 @@
 #pragma once
 
 #include "fft_core.cuh"
+#include "tma.cuh"
 
 namespace cubic {
 
@@ -44,15 +45,19 @@ struct XArgs {
     int64_t rows;      // nz * ny
     int64_t xp;        // spectrum pitch (complex elements)
     float eps;
+    unsigned *err;     // device error word (bounded waits)
 };
 
 struct YArgs {
     float2 *spec;
     const float2 *tw;
     int64_t nz;
-    int64_t xh;  // nx/2 + 1 valid columns
+    int64_t xh;    // nx/2 + 1 valid columns
     int64_t xp;
     int inverse;
+    int64_t col0;  // first column of this launch (multiple of the tile width)
+    int64_t col1;  // one past the last column (<= xh)
+    unsigned *err;
 };
 
 enum ZMode : int { ZM_FWD_SCALE = 0, ZM_CONV = 1, ZM_CORR = 2, ZM_INV_SCALE = 3 };
@@ -65,7 +70,11 @@ struct ZArgs {
     int64_t xh;
     int64_t xp;
     int mode;
-    float scale;  // ZM_FWD_SCALE / ZM_INV_SCALE only
+    float scale;   // ZM_FWD_SCALE / ZM_INV_SCALE only
+    int64_t col0;  // column range of this launch, as in YArgs
+    int64_t col1;
+    unsigned *err;
+    int64_t nz;    // lines are this long (TMA path builds its tensor map from it)
 };
 
 // ------------------------------------------------------------------ X pass
@@ -84,19 +93,58 @@ struct SmemStrided {  // element pos at base[pos * stride]
 template <int N>
 constexpr int x_smem_line() { return N + (N >> 5) + 1; }
 
+// The pointwise operand rows (d for the ratio, u for the update) are staged
+// into shared memory by one bulk TMA copy per CTA issued at kernel start, so
+// their HBM latency hides behind the inverse transform.  Needs 16-byte rows.
+template <int N, int MODE>
+constexpr bool x_uses_tma()
+{
+    return (MODE == XM_RATIO || MODE == XM_UPDATE || MODE == XM_FINAL) && (N % 4 == 0);
+}
+
+template <int N, int L, int MODE>
+constexpr size_t x_smem_bytes()
+{
+    return 16 + (x_uses_tma<N, MODE>() ? (size_t)L * 2 * N * sizeof(float) : 0) +
+           (size_t)L * x_smem_line<N>() * sizeof(float2);
+}
+
 template <int N, int P, int L, int MODE>
 __global__ void __launch_bounds__(P * L) k_xpass(XArgs a)
 {
     constexpr int E = N / P;
-    extern __shared__ float2 smem_x[];
+    constexpr bool kTma = x_uses_tma<N, MODE>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    float *oprows = reinterpret_cast<float *>(smem_raw + 16);
+    float2 *xch = reinterpret_cast<float2 *>(smem_raw + 16 + (kTma ? (size_t)L * 2 * N * sizeof(float) : 0));
+
     const int t = threadIdx.x % P;
     const int l = threadIdx.x / P;
     const int64_t m = (int64_t)blockIdx.x * L + l;
     const int64_t r0 = 2 * m, r1 = 2 * m + 1;
     const bool ok0 = r0 < a.rows, ok1 = r1 < a.rows;
-    SmemPadded sm{smem_x + l * x_smem_line<N>()};
+    SmemPadded sm{xch + l * x_smem_line<N>()};
     auto sync = [] { __syncthreads(); };
     using FFT = LineFFT<N, P>;
+
+    if constexpr (kTma) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // this CTA's rows are contiguous: one copy
+            const int64_t row0 = (int64_t)blockIdx.x * L * 2;
+            const int64_t left = a.rows - row0;
+            const int64_t nrows = left < 2 * L ? left : 2 * L;
+            const float *src = (MODE == XM_RATIO ? a.d : a.u) + row0 * N;
+            const unsigned bytes = (unsigned)(nrows * N * sizeof(float));
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(oprows, src, bytes, bar);
+        }
+    }
 
     float2 v[E];
     if constexpr (MODE == XM_FWD) {
@@ -127,6 +175,19 @@ __global__ void __launch_bounds__(P * L) k_xpass(XArgs a)
         });
         FFT::inverse(v, sm, a.tw, t, sync);
 
+        // operand rows: shared memory (TMA) or global
+        const float *p0, *p1;
+        if constexpr (kTma) {
+            const bool arrived = mbar_wait_bounded(bar, 0, a.err);
+            if (!__syncthreads_and(arrived)) return;
+            p0 = oprows + (2 * l) * N;
+            p1 = oprows + (2 * l + 1) * N;
+        } else {
+            const float *g = (MODE == XM_RATIO) ? a.d : a.u;
+            p0 = g + r0 * N;
+            p1 = g + r1 * N;
+        }
+
         // pointwise step on the real rows (v.x = row r0, v.y = row r1)
         if constexpr (MODE == XM_INV) {
             float *o0 = a.dst + r0 * N, *o1 = a.dst + r1 * N;
@@ -137,24 +198,24 @@ __global__ void __launch_bounds__(P * L) k_xpass(XArgs a)
                 if (ok1) o1[n] = v[i].y;
             });
         } else if constexpr (MODE == XM_RATIO) {
-            const float *d0 = a.d + r0 * N, *d1 = a.d + r1 * N;
             const float eps = a.eps;
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
-                const float x0 = ok0 ? __fdiv_rn(__ldg(d0 + n), fmaxf(v[i].x, eps)) : 0.f;
-                const float x1 = ok1 ? __fdiv_rn(__ldg(d1 + n), fmaxf(v[i].y, eps)) : 0.f;
+                // fast division (max 2 ulp for denominators below 2^126; the
+                // clamp keeps them >= eps)
+                const float x0 = ok0 ? __fdividef(p0[n], fmaxf(v[i].x, eps)) : 0.f;
+                const float x1 = ok1 ? __fdividef(p1[n], fmaxf(v[i].y, eps)) : 0.f;
                 v[i] = make_float2(x0, x1);
             });
         } else if constexpr (MODE == XM_UPDATE || MODE == XM_FINAL) {
-            float *u0 = a.u + r0 * N, *u1 = a.u + r1 * N;
             float *o0 = (MODE == XM_UPDATE ? a.u : a.dst) + r0 * N;
             float *o1 = (MODE == XM_UPDATE ? a.u : a.dst) + r1 * N;
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
-                const float x0 = ok0 ? u0[n] * v[i].x : 0.f;
-                const float x1 = ok1 ? u1[n] * v[i].y : 0.f;
+                const float x0 = ok0 ? p0[n] * v[i].x : 0.f;
+                const float x1 = ok1 ? p1[n] * v[i].y : 0.f;
                 if (ok0) o0[n] = x0;
                 if (ok1) o1[n] = x1;
                 v[i] = make_float2(x0, x1);
@@ -195,8 +256,8 @@ __global__ void __launch_bounds__(P * B) k_ypass(YArgs a)
     extern __shared__ float2 smem_y[];
     const int b = threadIdx.x % B;
     const int t = threadIdx.x / B;
-    const int64_t col = (int64_t)blockIdx.x * B + b;
-    const bool ok = col < a.xh;
+    const int64_t col = a.col0 + (int64_t)blockIdx.x * B + b;
+    const bool ok = col < a.col1;
     float2 *base = a.spec + (int64_t)blockIdx.y * N * a.xp + col;
     SmemStrided sm{smem_y + b, B};
     auto sync = [] { __syncthreads(); };
@@ -225,8 +286,8 @@ __global__ void __launch_bounds__(P * B) k_zpass(ZArgs a)
     extern __shared__ float2 smem_z[];
     const int b = threadIdx.x % B;
     const int t = threadIdx.x / B;
-    const int64_t col = (int64_t)blockIdx.x * B + b;
-    const bool ok = col < a.xh;
+    const int64_t col = a.col0 + (int64_t)blockIdx.x * B + b;
+    const bool ok = col < a.col1;
     const int64_t zstride = a.ny * a.xp;
     const int64_t off = (int64_t)blockIdx.y * a.xp + col;
     float2 *base = a.spec + off;

@@ -1,11 +1,19 @@
-// registry.cuh -- per-length kernel table: for every supported axis length n
-// the X-pass variants, the Y pass and the Z pass compiled for that n, with the
-// launch shape each uses.
+// registry.cuh -- per-length kernel table.  For every supported axis length n
+// there are one or more compiled launch-shape variants of each pass:
+//   X pass: threads per line P and line pairs per CTA L (all five modes)
+//   Y / Z pass: threads per line P and adjacent columns per CTA B
+// Variant 0 is the default; the autotuner (tuner.cu) times the others on a
+// plan's own buffers and picks per pass.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "colpass_tma.cuh"
 #include "passes.cuh"
 
 namespace cubic {
@@ -14,31 +22,31 @@ using XLaunch = cudaError_t (*)(const XArgs &, cudaStream_t);
 using YLaunch = cudaError_t (*)(const YArgs &, cudaStream_t);
 using ZLaunch = cudaError_t (*)(const ZArgs &, cudaStream_t);
 
-struct AxisKernels {
-    int n = 0;
-    int x_threads = 0, x_lines = 0;  // X pass: threads per line, line pairs per CTA
-    int yz_threads = 0, yz_cols = 0; // Y/Z passes: threads per line, columns per CTA
-    XLaunch x[XM_COUNT] = {};
+constexpr int kMaxVariants = 6;
+
+struct XVariant {
+    int P = 0, L = 0;
+    XLaunch fn[XM_COUNT] = {};
+};
+
+struct YZVariant {
+    int P = 0, B = 0;
+    bool tma = false;  // persistent TMA-pipelined kernel
     YLaunch y = nullptr;
     ZLaunch z = nullptr;
+};
+
+struct AxisKernels {
+    int n = 0;
+    int nx = 0, nyz = 0;  // number of X and Y/Z variants
+    XVariant xv[kMaxVariants];
+    YZVariant yzv[kMaxVariants];
 };
 
 // Table lookup; nullptr if n has no kernels.
 const AxisKernels *find_axis(int64_t n);
 
-// Every supported length, ascending (for enumeration by callers).
-int supported_lengths(const int **out);
-
-// ------------------------------------------------------------------ shapes
-
-template <int N>
-struct AxisShape {
-    static constexpr int Emax = N >= 256 ? 32 : 40;
-    static constexpr int P = (N == 1) ? 1 : choose_threads(N, Emax);
-    static_assert(P > 0, "no thread split for this length");
-    static constexpr int XL = (P >= 128) ? 1 : 128 / P;  // line pairs per X CTA
-    static constexpr int B = 16;                           // columns per Y/Z CTA
-};
+// ------------------------------------------------------------------ launchers
 
 inline cudaError_t set_smem(const void *fn, size_t bytes)
 {
@@ -46,46 +54,196 @@ inline cudaError_t set_smem(const void *fn, size_t bytes)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int N, int MODE>
+template <int N, int P, int L, int MODE>
 cudaError_t launch_x(const XArgs &a, cudaStream_t st)
 {
-    using S = AxisShape<N>;
     const int64_t pairs = (a.rows + 1) / 2;
-    const int64_t grid = (pairs + S::XL - 1) / S::XL;
-    const size_t smem = sizeof(float2) * S::XL * x_smem_line<N>();
-    auto fn = k_xpass<N, S::P, S::XL, MODE>;
+    const int64_t grid = (pairs + L - 1) / L;
+    constexpr size_t smem = x_smem_bytes<N, L, MODE>();
+    auto fn = k_xpass<N, P, L, MODE>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (grid == 0) return cudaSuccess;
-    fn<<<(unsigned)grid, S::P * S::XL, smem, st>>>(a);
+    fn<<<(unsigned)grid, P * L, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int N>
+template <int N, int P, int B>
 cudaError_t launch_y(const YArgs &a, cudaStream_t st)
 {
-    using S = AxisShape<N>;
-    dim3 grid((unsigned)((a.xh + S::B - 1) / S::B), (unsigned)a.nz);
-    const size_t smem = sizeof(float2) * S::B * N;
-    auto fn = k_ypass<N, S::P, S::B>;
+    dim3 grid((unsigned)((a.col1 - a.col0 + B - 1) / B), (unsigned)a.nz);
+    constexpr size_t smem = sizeof(float2) * B * N;
+    auto fn = k_ypass<N, P, B>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
-    fn<<<grid, S::P * S::B, smem, st>>>(a);
+    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    fn<<<grid, P * B, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int N>
+template <int N, int P, int B>
 cudaError_t launch_z(const ZArgs &a, cudaStream_t st)
 {
-    using S = AxisShape<N>;
-    dim3 grid((unsigned)((a.xh + S::B - 1) / S::B), (unsigned)a.ny);
-    const size_t smem = sizeof(float2) * S::B * N;
-    auto fn = k_zpass<N, S::P, S::B>;
+    dim3 grid((unsigned)((a.col1 - a.col0 + B - 1) / B), (unsigned)a.ny);
+    constexpr size_t smem = sizeof(float2) * B * N;
+    auto fn = k_zpass<N, P, B>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
-    fn<<<grid, S::P * S::B, smem, st>>>(a);
+    fn<<<grid, P * B, smem, st>>>(a);
     return cudaGetLastError();
 }
+
+// ------------------------------------------------------------------ TMA column passes
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();  // defined in capi.cu
+
+// Tensor map over a [nz][ny][xp] complex array viewed as float32 [nz][ny][2 xp].
+inline cudaError_t encode_spectrum_map(CUtensorMap *tm, const void *base, int64_t nz, int64_t ny, int64_t xp,
+                                       int box0, int box1, int box2)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * xp), (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)(2 * xp * sizeof(float)), (cuuint64_t)(2 * xp * ny * sizeof(float))};
+    const cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, (cuuint32_t)box2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int N, int P, int B, int KIND>
+int col_grid_cap()
+{
+    static int cap = [] {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colpass_tma<N, P, B, KIND>, P * B,
+                                                      col_smem_bytes<N, B, KIND>());
+        return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    }();
+    return cap;
+}
+
+template <int N, int P, int B, int KIND>
+cudaError_t launch_col(const float2 *spec, const float2 *H, int64_t nz, int64_t ny, int64_t xp, int64_t col0,
+                       int64_t col1, int64_t outer, const float2 *tw, int mode, float scale, unsigned *err,
+                       cudaStream_t st)
+{
+    constexpr int R = box_rows(N);
+    constexpr size_t smem = col_smem_bytes<N, B, KIND>();
+    auto fn = k_colpass_tma<N, P, B, KIND>;
+    static cudaError_t attr = set_smem((const void *)fn, smem);
+    if (attr != cudaSuccess) return attr;
+    if (col0 % B != 0) return cudaErrorInvalidValue;
+    CUtensorMap tm_spec, tm_h;
+    cudaError_t e = (KIND == COL_Y) ? encode_spectrum_map(&tm_spec, spec, nz, ny, xp, 2 * B, R, 1)
+                                    : encode_spectrum_map(&tm_spec, spec, nz, ny, xp, 2 * B, 1, R);
+    if (e != cudaSuccess) return e;
+    if (KIND == COL_Z && H) {
+        e = encode_spectrum_map(&tm_h, H, nz, ny, xp, 2 * B, 1, R);
+        if (e != cudaSuccess) return e;
+    } else {
+        tm_h = tm_spec;
+    }
+    ColArgs c;
+    c.tw = tw;
+    c.ntiles_col = (col1 - col0 + B - 1) / B;
+    c.ntiles = c.ntiles_col * outer;
+    c.col_tile0 = col0 / B;
+    c.mode = mode;
+    c.scale = scale;
+    c.err = err;
+    if (c.ntiles == 0) return cudaSuccess;
+    const int64_t cap = col_grid_cap<N, P, B, KIND>();
+    const unsigned grid = (unsigned)(c.ntiles < cap ? c.ntiles : cap);
+    fn<<<grid, P * B, smem, st>>>(tm_spec, tm_h, c);
+    return cudaGetLastError();
+}
+
+template <int N, int P, int B>
+cudaError_t launch_y_tma(const YArgs &a, cudaStream_t st)
+{
+    return launch_col<N, P, B, COL_Y>(a.spec, nullptr, a.nz, N, a.xp, a.col0, a.col1, a.nz, a.tw, a.inverse, 1.f,
+                                      a.err, st);
+}
+
+template <int N, int P, int B>
+cudaError_t launch_z_tma(const ZArgs &a, cudaStream_t st)
+{
+    const bool needH = a.mode == ZM_CONV || a.mode == ZM_CORR;
+    return launch_col<N, P, B, COL_Z>(a.spec, needH ? a.H : nullptr, N, a.ny, a.xp, a.col0, a.col1, a.ny, a.tw,
+                                      a.mode, a.scale, a.err, st);
+}
+
+// Y and Z tile widths may differ: the Z pass also stages H.
+template <int N, int P, int BY, int BZ>
+YZVariant make_yzvariant_tma()
+{
+    YZVariant v;
+    v.P = P;
+    v.B = BY;
+    v.tma = true;
+    if constexpr (BY > 0)
+        v.y = launch_y_tma<N, P, BY>;
+    else
+        v.y = launch_y<N, P, 16>;
+    if constexpr (BZ > 0)
+        v.z = launch_z_tma<N, P, BZ>;
+    else
+        v.z = launch_z<N, P, 16>;
+    return v;
+}
+
+// widest column tile (16 or 8) whose double-buffered stages fit in 200 KB
+template <int N, int KIND>
+constexpr int tma_cols()
+{
+    return col_smem_bytes<N, 16, KIND>() <= 200 * 1024 ? 16 : col_smem_bytes<N, 8, KIND>() <= 200 * 1024 ? 8 : 0;
+}
+
+template <int N, int P, int L>
+XVariant make_xvariant()
+{
+    XVariant v;
+    v.P = P;
+    v.L = L;
+    v.fn[XM_FWD] = launch_x<N, P, L, XM_FWD>;
+    v.fn[XM_INV] = launch_x<N, P, L, XM_INV>;
+    v.fn[XM_RATIO] = launch_x<N, P, L, XM_RATIO>;
+    v.fn[XM_UPDATE] = launch_x<N, P, L, XM_UPDATE>;
+    v.fn[XM_FINAL] = launch_x<N, P, L, XM_FINAL>;
+    return v;
+}
+
+template <int N, int P, int B>
+YZVariant make_yzvariant()
+{
+    YZVariant v;
+    v.P = P;
+    v.B = B;
+    v.y = launch_y<N, P, B>;
+    v.z = launch_z<N, P, B>;
+    return v;
+}
+
+// ------------------------------------------------------------------ shapes
+
+// Default split: fewest radix stages with at most 32 (n >= 256) or 40 elements
+// per thread.  Alternative: at most 16 elements per thread (more threads, more
+// stages, fewer registers).
+template <int N>
+struct AxisShape {
+    static constexpr int P0 = (N == 1) ? 1 : choose_threads(N, N >= 256 ? 32 : 40);
+    static constexpr int P1 = (N == 1) ? 1 : choose_threads(N, 16);
+    static_assert(P0 > 0, "no thread split for this length");
+    static constexpr int lines(int P, int threads) { return P >= threads ? 1 : threads / P; }
+    // lengths that get tuned variants (the large, bandwidth-critical ones)
+    static constexpr bool kTuned = (N >= 64);
+    static constexpr bool kAlt = kTuned && P1 > 0 && P1 != P0 && P1 * 16 <= 1024;
+};
 
 template <int N>
 AxisKernels make_axis()
@@ -93,17 +251,26 @@ AxisKernels make_axis()
     using S = AxisShape<N>;
     AxisKernels k;
     k.n = N;
-    k.x_threads = S::P;
-    k.x_lines = S::XL;
-    k.yz_threads = S::P;
-    k.yz_cols = S::B;
-    k.x[XM_FWD] = launch_x<N, XM_FWD>;
-    k.x[XM_INV] = launch_x<N, XM_INV>;
-    k.x[XM_RATIO] = launch_x<N, XM_RATIO>;
-    k.x[XM_UPDATE] = launch_x<N, XM_UPDATE>;
-    k.x[XM_FINAL] = launch_x<N, XM_FINAL>;
-    k.y = launch_y<N>;
-    k.z = launch_z<N>;
+    constexpr int P0 = S::P0;
+    k.xv[0] = make_xvariant<N, P0, S::lines(P0, 128)>();
+    k.nx = 1;
+    k.nyz = 0;
+    constexpr int BY = tma_cols<N, COL_Y>(), BZ = tma_cols<N, COL_Z>();
+    if constexpr (S::kTuned && (BY > 0 || BZ > 0)) {
+        // TMA-pipelined variants first: they are the defaults where they exist
+        k.yzv[k.nyz++] = make_yzvariant_tma<N, P0, BY, BZ>();
+        if constexpr (S::P1 > 0 && S::P1 != P0 && S::P1 * (BY > BZ ? BY : BZ) <= 1024 && S::P1 * 16 <= 1024)
+            k.yzv[k.nyz++] = make_yzvariant_tma<N, S::P1, BY, BZ>();
+    }
+    k.yzv[k.nyz++] = make_yzvariant<N, P0, 16>();
+    if constexpr (S::kTuned) {
+        k.yzv[k.nyz++] = make_yzvariant<N, P0, 8>();
+        if constexpr (S::kAlt) {
+            constexpr int P1 = S::P1;
+            k.xv[k.nx++] = make_xvariant<N, P1, S::lines(P1, 128)>();
+            k.yzv[k.nyz++] = make_yzvariant<N, P1, 8>();
+        }
+    }
     return k;
 }
 
@@ -114,7 +281,7 @@ constexpr int kLengths[] = {1,   2,   3,   4,   5,   6,   8,   9,   10,  12,  15
                             81,  90,  96,  100, 108, 120, 125, 128, 135, 144, 150, 160, 192, 256, 320,
                             384, 512, 640, 768, 1024};
 constexpr int kNumLengths = sizeof(kLengths) / sizeof(kLengths[0]);
-constexpr int kShards = 8;
+constexpr int kShards = 16;
 
 // Fill table entries of shard S (defined in kernels_shard.cuh).
 template <int S>

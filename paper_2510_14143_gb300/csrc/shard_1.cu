@@ -1,3 +1,3 @@
-// Kernel instantiations, build shard 1 (lengths with index % 8 == 1).
+// Kernel instantiations, build shard 1 (lengths with index % 16 == 1).
 #define CUBIC_SHARD 1
 #include "kernels_shard.cuh"

@@ -1,3 +1,3 @@
-// Kernel instantiations, build shard 2 (lengths with index % 8 == 2).
+// Kernel instantiations, build shard 2 (lengths with index % 16 == 2).
 #define CUBIC_SHARD 2
 #include "kernels_shard.cuh"

@@ -1,3 +1,3 @@
-// Kernel instantiations, build shard 4 (lengths with index % 8 == 4).
+// Kernel instantiations, build shard 4 (lengths with index % 16 == 4).
 #define CUBIC_SHARD 4
 #include "kernels_shard.cuh"

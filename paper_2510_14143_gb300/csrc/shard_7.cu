@@ -1,3 +1,3 @@
-// Kernel instantiations, build shard 7 (lengths with index % 8 == 7).
+// Kernel instantiations, build shard 7 (lengths with index % 16 == 7).
 #define CUBIC_SHARD 7
 #include "kernels_shard.cuh"

@@ -196,3 +196,65 @@ def test_errors_are_reported(cr):
     with pytest.raises(cr.CubicError) as e:
         cr.cubic_rl_plan((4, 4, 7), dev(np.ones((4, 4, 7), np.float32)))
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("shape", [(64, 96, 128), (128, 80, 64), (16, 256, 100), (8, 1024, 1024)])
+def test_every_launch_variant_matches_oracle(cr, shape):
+    # each compiled launch shape of each pass computes the same convolution
+    r = np.random.default_rng(sum(shape))
+    psf = r.uniform(0.1, 1.0, shape).astype(np.float32) ** 3
+    psf /= psf.sum()
+    x = synth.random_field(shape, seed=11 + sum(shape))
+    plan = cr.cubic_rl_plan(shape, dev(psf))
+    (nx, ny, nz), _ = cr.cubic_rl_plan_variants(plan)
+    ref = oracle.convolve(oracle.psf_spectrum(psf.astype(np.float64)), x.astype(np.float64), True)
+    xd = dev(x)
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    combos = {(vx, 0, 0) for vx in range(nx)} | {(0, vy, 0) for vy in range(ny)} | {(0, 0, vz) for vz in range(nz)}
+    for vx, vy, vz in sorted(combos):
+        cr.cubic_rl_plan_set_variants(plan, vx, vy, vz)
+        cr.cubic_rl_convolve(plan, xd, True, out)
+        torch.cuda.synchronize()
+        assert rel_l2(out.cpu().numpy(), ref) < 1e-5, (vx, vy, vz)
+    with pytest.raises(cr.CubicError):
+        cr.cubic_rl_plan_set_variants(plan, nx, 0, 0)
+
+
+def test_autotune_keeps_results(cr):
+    w = synth.SMALL
+    d, _ = synth.workload_volume(w)
+    psf = oracle.psf_gaussian(d.shape, w.psf_sigma_xy, w.psf_sigma_z).astype(np.float32)
+    plan = cr.cubic_rl_plan(d.shape, dev(psf))
+    dd = dev(d)
+    out = torch.empty_like(dd)
+    cr.cubic_rl_autotune(plan, dd, out)
+    counts, chosen = cr.cubic_rl_plan_variants(plan)
+    assert all(0 <= c < n for c, n in zip(chosen, counts))
+    cr.cubic_rl_deconvolve(plan, dd, w.n_iter, 1e-6, out)
+    cr.cubic_rl_stream_status(plan)
+    ref = oracle.rl(d, psf, w.n_iter, 1e-6)
+    assert rel_l2(out.cpu().numpy(), ref) <= 1e-4
+    # a later plan of the same dims starts from the tuned choice
+    plan2 = cr.cubic_rl_plan(d.shape, dev(psf))
+    assert cr.cubic_rl_plan_variants(plan2)[1] == chosen
+
+
+def test_host_buffer_entry_point(cr):
+    w = synth.SMALL
+    d, _ = synth.workload_volume(w)
+    psf = oracle.psf_gaussian(d.shape, w.psf_sigma_xy, w.psf_sigma_z).astype(np.float32)
+    plan = cr.cubic_rl_plan(d.shape, dev(psf))
+    out = np.empty_like(d)
+    cr.cubic_rl_deconvolve_host(plan, np.ascontiguousarray(d), 7, 1e-6, out)
+    torch.cuda.synchronize()
+    ref = oracle.rl(d, psf, 7, 1e-6)
+    assert rel_l2(out, ref) <= 1e-4
+
+
+def test_psf_gaussian_kernel_matches_oracle(cr):
+    for shape, sxy, sz, amp in [((32, 64, 64), 1.5, 3.0, 1.0), ((9, 12, 11), 1.7, 2.6, 1.3), ((5, 1, 7), 0.8, 2.0, 2.0)]:
+        psf = torch.empty(shape, dtype=torch.float32, device="cuda")
+        cr.cubic_psf_gaussian(shape, sxy, sz, amp, psf)
+        torch.cuda.synchronize()
+        ref = oracle.psf_gaussian(shape, sxy, sz, amp)
+        assert np.allclose(psf.cpu().numpy(), ref, rtol=2e-6, atol=1e-9 * amp)
