@@ -155,6 +155,10 @@ def run_ours(args, w: synth.Workload):
     plan = cr.cubic_rl_plan(shape, psf)
     out = torch.empty_like(d)
     stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    cr.cubic_rl_autotune(plan, d, out)          # untimed, like plan creation
+    tune_s = time.perf_counter() - t0
+    variants = cr.cubic_rl_plan_variants(plan)
 
     for _ in range(args.warmup):
         cr.cubic_rl_deconvolve(plan, d, n_iter, eps, out)
@@ -226,6 +230,7 @@ def run_ours(args, w: synth.Workload):
                         "GBps": round(v["bytes"] / v["launches"] / (v["ms"] / v["timed"] * 1e-3) / 1e9, 1)}
                     for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["ms"])},
         "flux_rel_err": flux_rel,
+        "tuning": {"variants_xyz": list(variants[1]), "of": list(variants[0]), "seconds": round(tune_s, 2)},
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
