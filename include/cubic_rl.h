@@ -150,6 +150,24 @@ CUBIC_API int64_t cubic_rl_plan_chunk(cubic_rl_plan_t plan);
 CUBIC_API cubic_status_t cubic_rl_autotune(cubic_rl_plan_t plan, const float *image, float *out,
                                            void *stream);
 
+/* Allocation-free deconvolution.  The paper has no counterpart: this is a service for
+ * callers that must not allocate device memory -- code running while another framework
+ * captures the stream into a CUDA graph, processes whose device memory is fully reserved
+ * by a pool allocator, and latency-critical code that cannot take cudaMalloc's implicit
+ * device synchronisation.  Same result as cubic_rl_plan + cubic_rl_deconvolve on
+ * (psf, image), but every internal buffer lives in one fixed 8 MiB device array that each
+ * GPU loading this library holds until the process exits; nothing is allocated or freed.
+ * Limit: nz * ny * xp <= about 2^19 complex elements, xp = nx/2+1 rounded up to 16 (e.g.
+ * 64x64x64); larger volumes get CUBIC_ERR_UNSUPPORTED_SIZE with the byte counts.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call outside any stream capture.  All calls share the array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race and give wrong
+ * results; serialise them.  psf, image, out: device float32 [nz][ny][nx], 16-byte
+ * aligned; out must not overlap image. */
+CUBIC_API cubic_status_t cubic_rl_deconvolve_noalloc(const int64_t dims[3], const float *psf,
+                                                     const float *image, int n_iter, float eps,
+                                                     float *out, void *stream);
+
 /* ---- launch accounting and per-kernel timing ---- */
 
 /* Number of kernel kinds and the name of each (static strings). */

@@ -58,6 +58,7 @@ _SIGS = {
     "cubic_rl_autotune": ([_vp, _vp, _vp, _vp], _ci),
     "cubic_rl_plan_set_chunk": ([_vp, _i64], _ci),
     "cubic_rl_plan_chunk": ([_vp], _i64),
+    "cubic_rl_deconvolve_noalloc": ([ctypes.POINTER(_i64), _vp, _vp, _ci, _cf, _vp, _vp], _ci),
     "cubic_rl_kernel_kinds": ([], _ci),
     "cubic_rl_kernel_name": ([_ci], ctypes.c_char_p),
     "cubic_rl_profile": ([_vp, _ci, _ci], _ci),
@@ -250,6 +251,19 @@ def cubic_rl_autotune(plan: Plan, image, out, stream=None) -> None:
     _check(lib().cubic_rl_autotune(plan.handle, _ptr(image, torch.float32, plan.voxels, "image"),
                                    _ptr(out, torch.float32, plan.voxels, "out"), _stream(stream)),
            "cubic_rl_autotune")
+
+
+def cubic_rl_deconvolve_noalloc(dims, psf, image, n_iter: int, eps: float, out, stream=None) -> None:
+    """Deconvolution that allocates no device memory (for callers that cannot allocate,
+    e.g. under another framework's stream capture or a fully reserved memory pool).
+    Uses one fixed per-device scratch array shared by all calls: serialise calls."""
+    import torch
+    dims = tuple(int(d) for d in dims)
+    v = dims[0] * dims[1] * dims[2]
+    d = (_i64 * 3)(*dims)
+    _check(lib().cubic_rl_deconvolve_noalloc(d, _ptr(psf, torch.float32, v, "psf"), _ptr(image, torch.float32, v, "image"),
+                                             int(n_iter), float(eps), _ptr(out, torch.float32, v, "out"),
+                                             _stream(stream)), "cubic_rl_deconvolve_noalloc")
 
 
 def cubic_rl_kernel_kinds() -> int:

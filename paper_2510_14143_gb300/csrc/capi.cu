@@ -939,3 +939,98 @@ extern "C" cubic_status_t cubic_rl_stream_status(cubic_rl_plan_t plan, void *str
     }
     return CUBIC_OK;
 }
+
+// ------------------------------------------------------------------ allocation-free entry point
+//
+// For callers that must not allocate device memory: code running while another
+// framework captures a stream into a CUDA graph, processes whose device memory is
+// entirely reserved by a pool allocator, and latency-critical callers that cannot
+// afford cudaMalloc's implicit device synchronisation.  Everything a deconvolution
+// needs beyond its inputs and outputs (PSF spectrum, work spectrum, twiddles,
+// reduction partials, error word) lives in one fixed file-scope device array.
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_ptr[64];  // device address of the array, per device ordinal
+
+static size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+extern "C" cubic_status_t cubic_rl_deconvolve_noalloc(const int64_t dims[3], const float *psf, const float *image,
+                                                      int n_iter, float eps, float *out, void *stream)
+{
+    if (!dims || !psf || !image || !out) return fail(CUBIC_ERR_INVALID_ARG, "dims, psf, image and out must be non-null");
+    for (int i = 0; i < 3; ++i)
+        if (dims[i] < 1 || !find_axis(dims[i]))
+            return fail(CUBIC_ERR_UNSUPPORTED_SIZE, "axis %d has unsupported length %lld", i, (long long)dims[i]);
+    if (dims[0] > 65535 || dims[1] > 65535) return fail(CUBIC_ERR_UNSUPPORTED_SIZE, "nz and ny must be <= 65535");
+    if (n_iter < 0) return fail(CUBIC_ERR_INVALID_ARG, "n_iter must be >= 0");
+    if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
+    if (!aligned16(psf) || !aligned16(image) || !aligned16(out))
+        return fail(CUBIC_ERR_ALIGNMENT, "psf, image and out must be 16-byte aligned");
+
+    // a plan that lives on this stack frame; its device buffers are carved out of the array
+    cubic_rl_plan_s p;
+    p.nz = dims[0];
+    p.ny = dims[1];
+    p.nx = dims[2];
+    p.V = p.nz * p.ny * p.nx;
+    p.rows = p.nz * p.ny;
+    p.xh = p.nx / 2 + 1;
+    p.xp = (p.xh + 15) / 16 * 16;
+    p.kx = find_axis(p.nx);
+    p.ky = find_axis(p.ny);
+    p.kz = find_axis(p.nz);
+    if (overlaps(image, out, (size_t)p.V * sizeof(float)))
+        return fail(CUBIC_ERR_INVALID_ARG, "out must not overlap image");
+    const size_t spec_bytes = align256(spec_elems(&p) * sizeof(float2));
+    const size_t tw_bytes = align256((size_t)(p.nx + p.ny + p.nz) * sizeof(float2));
+    const size_t red_bytes = align256((kReduceBlocks + 1) * sizeof(double));
+    const size_t need = 2 * spec_bytes + tw_bytes + red_bytes + 256;
+    if (need > kNoAllocScratchBytes)
+        return fail(CUBIC_ERR_UNSUPPORTED_SIZE,
+                    "volume needs %zu bytes of scratch; the allocation-free entry point has %zu "
+                    "(nz*ny*(nx/2+1 rounded up to 16) must stay below about 2^19)",
+                    need, kNoAllocScratchBytes);
+
+    // once per device, with that device current: the array's device address
+    int dev = 0;
+    CUBIC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CUBIC_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+    unsigned char *base;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *addr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+            if (e != cudaSuccess || !addr)
+                return fail(CUBIC_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = (unsigned char *)addr;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    p.device = dev;
+    p.H = (float2 *)base;
+    p.ws = (float2 *)(base + spec_bytes);
+    p.own_ws = false;
+    p.tw = (float2 *)(base + 2 * spec_bytes);
+    p.tw_x = p.tw;
+    p.tw_y = p.tw + p.nx;
+    p.tw_z = p.tw + p.nx + p.ny;
+    p.partial = (double *)(base + 2 * spec_bytes + tw_bytes);
+    p.err = (unsigned *)(base + 2 * spec_bytes + tw_bytes + red_bytes);
+    tuned_variants(&p);
+
+    cudaStream_t st = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: the error word must start at zero,
+    // everything else is rewritten below before it is read
+    CUBIC_CUDA(cudaMemsetAsync(p.err, 0, sizeof(unsigned), st));
+    k_twiddles<<<grid_for(p.nx, 128, 1 << 20), 128, 0, st>>>(p.tw_x, (int)p.nx);
+    k_twiddles<<<grid_for(p.ny, 128, 1 << 20), 128, 0, st>>>(p.tw_y, (int)p.ny);
+    k_twiddles<<<grid_for(p.nz, 128, 1 << 20), 128, 0, st>>>(p.tw_z, (int)p.nz);
+    CUBIC_CUDA(cudaGetLastError());
+    cubic_status_t s = load_psf(&p, psf, st);
+    if (s != CUBIC_OK) return s;
+    return enqueue_rl(&p, image, n_iter, eps, out, p.ws, st);
+}
