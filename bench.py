@@ -327,6 +327,22 @@ def run_reference(args, w: synth.Workload):
     return rank, result
 
 
+def run_ncu_target(args, w: synth.Workload):
+    """Profiling target: plan + one RL iteration with pinned launch shapes; no timing, no line."""
+    import torch
+    import paper_2510_14143_gb300 as cr
+    vx, vy, vz = (int(v) for v in args.ncu_target.split(","))
+    g = torch.Generator(device="cuda").manual_seed(1)
+    d = torch.rand(w.shape, device="cuda", generator=g) * 100 + 1
+    psf = torch.empty(w.shape, dtype=torch.float32, device="cuda")
+    cr.cubic_psf_gaussian(w.shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0, psf)
+    plan = cr.cubic_rl_plan(w.shape, psf)
+    cr.cubic_rl_plan_set_variants(plan, vx, vy, vz)
+    out = torch.empty_like(d)
+    cr.cubic_rl_deconvolve(plan, d, args.ncu_iters, 1e-6, out)
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,8 +352,14 @@ def main():
     ap.add_argument("--workload", choices=sorted(synth.PLAIN), default=synth.LARGE.name)
     ap.add_argument("--cpu-sample", choices=("crop", "full"), default="full")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-target", metavar="VX,VY,VZ",
+                    help="profiling target only: plan + --ncu-iters RL iterations with these launch shapes")
+    ap.add_argument("--ncu-iters", type=int, default=1)
     args = ap.parse_args()
     w = synth.PLAIN[args.workload]
+    if args.ncu_target:
+        run_ncu_target(args, w)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     rank, result = run_reference(args, w) if args.impl == "reference" else run_ours(args, w)
