@@ -233,11 +233,56 @@ def run_ours(args, w: synth.Workload):
         "tuning": {"variants_xyz": list(variants[1]), "of": list(variants[0]), "seconds": round(tune_s, 2)},
         "clocks": clk,
     }
+    if not args.no_batched:
+        result["batched"] = run_batched(cr, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, d_host, args.cpu_sample)
     if dist is not None:
         dist.destroy_process_group()
     return rank, result
+
+
+def run_batched(cr, args):
+    """64 uneven volumes (5-smooth axes in [48,160]) x 50 iterations: one graph vs 64 plain calls."""
+    import torch
+    shapes = synth.batch_shapes()
+    plans, imgs, outs = [], [], []
+    for j, shape in enumerate(shapes):
+        d, _ = synth.batch_volume(j, shape)
+        psf = torch.empty(shape, dtype=torch.float32, device="cuda")
+        cr.cubic_psf_gaussian(shape, synth.SMALL.psf_sigma_xy, synth.SMALL.psf_sigma_z, 1.0, psf)
+        plans.append(cr.cubic_rl_plan(shape, psf))
+        imgs.append(torch.from_numpy(d).cuda())
+        outs.append(torch.empty(shape, dtype=torch.float32, device="cuda"))
+    n_iter, eps = synth.BATCH_ITERS, 1e-6
+    vox = sum(int(np.prod(s)) for s in shapes)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(1, min(args.steps, 5))
+    ms_b = timed(lambda: cr.cubic_rl_deconvolve_batched(plans, imgs, n_iter, eps, outs), reps)
+    nodes = cr.cubic_rl_batched_graph_nodes()
+
+    def plain():
+        for p, i, o in zip(plans, imgs, outs):
+            cr.cubic_rl_deconvolve(p, i, n_iter, eps, o)
+
+    ms_p = timed(plain, reps)
+    return {"workload": f"{len(shapes)} volumes, axes drawn from the 5-smooth lengths in [48,160], {n_iter} iterations",
+            "voxels": vox, "value": round(vox * n_iter / (ms_b * 1e-3) / 1e9, 3), "unit": UNIT,
+            "ms": round(ms_b, 3), "graph_kernel_nodes": nodes, "plain_calls_ms": round(ms_p, 3),
+            "speedup_vs_plain_calls": round(ms_p / ms_b, 3)}
 
 
 def load_traffic(kernel: str, w: synth.Workload):
@@ -352,6 +397,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(synth.PLAIN), default=synth.LARGE.name)
     ap.add_argument("--cpu-sample", choices=("crop", "full"), default="full")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--ncu-target", metavar="VX,VY,VZ",
                     help="profiling target only: plan + --ncu-iters RL iterations with these launch shapes")
     ap.add_argument("--ncu-iters", type=int, default=1)

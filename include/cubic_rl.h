@@ -100,6 +100,21 @@ CUBIC_API cubic_status_t cubic_rl_set_workspace(cubic_rl_plan_t plan, void *dev_
 CUBIC_API cubic_status_t cubic_rl_deconvolve(cubic_rl_plan_t plan, const float *image, int n_iter, float eps,
                                    float *out, void *stream);
 
+/* Batched Richardson-Lucy: the same deconvolution as cubic_rl_deconvolve for n volumes of
+ * possibly different sizes, each with its own plan (plans must be distinct: a plan's scratch
+ * serves one volume).  images[v], outs[v]: device float32 volumes of plans[v]'s dims.  For
+ * each pass, all volumes with the same length along that pass share one kernel launch whose
+ * blocks span every member volume; the whole n_iter sequence is captured once into a CUDA
+ * graph (first call with a given argument set: capture + instantiation, synchronous) and
+ * replayed on `stream` by later calls with identical arguments (a few argument sets are
+ * cached).  1 <= n <= 256.  Errors: INVALID_ARG, ALIGNMENT, OUT_OF_MEMORY, CUDA. */
+CUBIC_API cubic_status_t cubic_rl_deconvolve_batched(const cubic_rl_plan_t *plans, int n,
+                                                     const float *const *images, int n_iter, float eps,
+                                                     float *const *outs, void *stream);
+
+/* Kernel nodes in the graph the last cubic_rl_deconvolve_batched call replayed. */
+CUBIC_API int64_t cubic_rl_batched_graph_nodes(void);
+
 /* cubic_rl_deconvolve on host buffers: copies `image` (host, V floats; pinned memory makes
  * the copies asynchronous) to device memory owned by the plan, deconvolves there, and
  * copies the estimate back into `out` (host, V floats).  All three steps are enqueued on

@@ -59,6 +59,9 @@ _SIGS = {
     "cubic_rl_plan_set_chunk": ([_vp, _i64], _ci),
     "cubic_rl_plan_chunk": ([_vp], _i64),
     "cubic_rl_deconvolve_noalloc": ([ctypes.POINTER(_i64), _vp, _vp, _ci, _cf, _vp, _vp], _ci),
+    "cubic_rl_deconvolve_batched": ([ctypes.POINTER(_vp), _ci, ctypes.POINTER(_vp), _ci, _cf, ctypes.POINTER(_vp),
+                                     _vp], _ci),
+    "cubic_rl_batched_graph_nodes": ([], _i64),
     "cubic_rl_kernel_kinds": ([], _ci),
     "cubic_rl_kernel_name": ([_ci], ctypes.c_char_p),
     "cubic_rl_profile": ([_vp, _ci, _ci], _ci),
@@ -264,6 +267,23 @@ def cubic_rl_deconvolve_noalloc(dims, psf, image, n_iter: int, eps: float, out, 
     _check(lib().cubic_rl_deconvolve_noalloc(d, _ptr(psf, torch.float32, v, "psf"), _ptr(image, torch.float32, v, "image"),
                                              int(n_iter), float(eps), _ptr(out, torch.float32, v, "out"),
                                              _stream(stream)), "cubic_rl_deconvolve_noalloc")
+
+
+def cubic_rl_deconvolve_batched(plans, images, n_iter: int, eps: float, outs, stream=None) -> None:
+    """Deconvolve len(plans) volumes (one plan each, distinct) as one CUDA graph."""
+    import torch
+    n = len(plans)
+    if len(images) != n or len(outs) != n:
+        raise ValueError("plans, images and outs must have the same length")
+    P = (_vp * n)(*[p.handle for p in plans])
+    I = (_vp * n)(*[_ptr(im, torch.float32, p.voxels, "image") for im, p in zip(images, plans)])
+    O = (_vp * n)(*[_ptr(o, torch.float32, p.voxels, "out") for o, p in zip(outs, plans)])
+    _check(lib().cubic_rl_deconvolve_batched(P, n, I, int(n_iter), float(eps), O, _stream(stream)),
+           "cubic_rl_deconvolve_batched")
+
+
+def cubic_rl_batched_graph_nodes() -> int:
+    return int(lib().cubic_rl_batched_graph_nodes())
 
 
 def cubic_rl_kernel_kinds() -> int:

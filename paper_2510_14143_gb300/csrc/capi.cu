@@ -10,6 +10,8 @@
 
 #include <stdlib.h>
 
+#include <algorithm>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -535,11 +537,9 @@ static bool overlaps(const void *a, const void *b, size_t n)
     return x < y + n && y < x + n;
 }
 
-// The n_iter-iteration sequence, enqueued on `st`.
-static cubic_status_t enqueue_rl(cubic_rl_plan_s *p, const float *image, int n_iter, float eps, float *out,
-                                 float2 *spec, cudaStream_t st)
+// u0 = max(mean(image), eps) into out.
+static cubic_status_t enqueue_init(cubic_rl_plan_s *p, const float *image, float eps, float *out, cudaStream_t st)
 {
-    // u0 = max(mean(image), eps)
     CUBIC_CUDA(counted(p, KK_SUM, st, [&] {
         k_sum_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(image, p->V, p->partial);
         k_sum_final<<<1, kReduceThreads, 0, st>>>(p->partial, kReduceBlocks, p->partial + kReduceBlocks);
@@ -550,6 +550,15 @@ static cubic_status_t enqueue_rl(cubic_rl_plan_s *p, const float *image, int n_i
         k_fill_initial<<<grid_for(p->V, 256), 256, 0, st>>>(out, p->V, p->partial + kReduceBlocks, eps);
         return cudaGetLastError();
     }));
+    return CUBIC_OK;
+}
+
+// The n_iter-iteration sequence, enqueued on `st`.
+static cubic_status_t enqueue_rl(cubic_rl_plan_s *p, const float *image, int n_iter, float eps, float *out,
+                                 float2 *spec, cudaStream_t st)
+{
+    cubic_status_t s0 = enqueue_init(p, image, eps, out, st);
+    if (s0 != CUBIC_OK) return s0;
     if (n_iter == 0) return CUBIC_OK;
 
     XArgs xa = x_args(p);
@@ -938,6 +947,244 @@ extern "C" cubic_status_t cubic_rl_stream_status(cubic_rl_plan_t plan, void *str
         return fail(CUBIC_ERR_TIMEOUT, "a device wait timed out (error word 0x%x)", word);
     }
     return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ batched deconvolution
+//
+// Many volumes of different sizes in one CUDA graph.  For every pass, the volumes
+// whose axis along that pass has the same length share one launch: the launch's
+// blocks are the concatenation of every member volume's blocks, and each block
+// finds its volume in a device-side table (k_*_multi).  The whole n_iter sequence
+// is captured once into a graph and replayed on later calls with the same
+// arguments.
+
+namespace {
+
+struct XGroup {
+    const AxisKernels *k;
+    MultiTable<XArgs> *tab;
+    int64_t blocks;
+};
+struct YGroup {
+    const AxisKernels *k;
+    MultiTable<YArgs> *tab;
+    int64_t blocks;
+};
+struct ZGroup {
+    const AxisKernels *k;
+    MultiTable<ZArgs> *tab;
+    int64_t blocks;
+};
+
+struct BatchState {
+    std::vector<cubic_rl_plan_s *> plans;
+    std::vector<const float *> images;
+    std::vector<float *> outs;
+    int n_iter = 0;
+    float eps = 0.f;
+    std::vector<XGroup> gx;
+    std::vector<YGroup> gy;
+    std::vector<ZGroup> gz;
+    void *dmem = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t kernel_nodes = 0;
+    ~BatchState()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (dmem) cudaFree(dmem);
+    }
+};
+
+std::mutex g_batch_mu;
+std::vector<BatchState *> g_batches;  // most recent last; a few kept
+int64_t g_batch_last_nodes = 0;
+
+}  // namespace
+
+static cubic_status_t enqueue_batched(BatchState &b, cudaStream_t st)
+{
+    for (size_t v = 0; v < b.plans.size(); ++v) {
+        cubic_status_t s = enqueue_init(b.plans[v], b.images[v], b.eps, b.outs[v], st);
+        if (s != CUBIC_OK) return s;
+    }
+    if (b.n_iter == 0) return CUBIC_OK;
+    auto xstage = [&](int mode) -> cubic_status_t {
+        for (const XGroup &g : b.gx) CUBIC_CUDA(g.k->xm[mode](g.tab, g.blocks, st));
+        return CUBIC_OK;
+    };
+    auto yzy = [&](int zmode) -> cubic_status_t {
+        for (const YGroup &g : b.gy) CUBIC_CUDA(g.k->ym(g.tab, g.blocks, 0, st));
+        for (const ZGroup &g : b.gz) CUBIC_CUDA(g.k->zm(g.tab, g.blocks, zmode, st));
+        for (const YGroup &g : b.gy) CUBIC_CUDA(g.k->ym(g.tab, g.blocks, 1, st));
+        return CUBIC_OK;
+    };
+    cubic_status_t s = xstage(XM_FWD);
+    for (int k = 0; k < b.n_iter && s == CUBIC_OK; ++k) {
+        if ((s = yzy(ZM_CONV)) != CUBIC_OK) break;
+        if ((s = xstage(XM_RATIO)) != CUBIC_OK) break;
+        if ((s = yzy(ZM_CORR)) != CUBIC_OK) break;
+        s = xstage(k + 1 < b.n_iter ? XM_UPDATE : XM_FINAL);
+    }
+    return s;
+}
+
+// Group volumes by axis length and build the device tables.
+static cubic_status_t build_batch(BatchState &b)
+{
+    const int n = (int)b.plans.size();
+    std::map<int64_t, std::vector<int>> byx, byy, byz;
+    for (int v = 0; v < n; ++v) {
+        byx[b.plans[v]->nx].push_back(v);
+        byy[b.plans[v]->ny].push_back(v);
+        byz[b.plans[v]->nz].push_back(v);
+    }
+    const size_t ntab = byx.size() + byy.size() + byz.size();
+    const size_t tsz = std::max({sizeof(MultiTable<XArgs>), sizeof(MultiTable<YArgs>), sizeof(MultiTable<ZArgs>)});
+    const size_t stride = (tsz + 255) / 256 * 256;
+    std::vector<unsigned char> host(stride * ntab, 0);
+    CUBIC_CUDA(cudaMalloc(&b.dmem, host.size()));
+    unsigned char *dbase = (unsigned char *)b.dmem;
+    size_t slot = 0;
+    for (auto &kv : byx) {
+        auto *t = reinterpret_cast<MultiTable<XArgs> *>(host.data() + slot * stride);
+        const AxisKernels *k = find_axis(kv.first);
+        t->nvol = (int)kv.second.size();
+        int64_t blocks = 0;
+        for (int i = 0; i < t->nvol; ++i) {
+            cubic_rl_plan_s *p = b.plans[kv.second[i]];
+            XArgs a = x_args(p);
+            a.spec_in = p->ws;
+            a.spec_out = p->ws;
+            a.src = b.outs[kv.second[i]];
+            a.u = b.outs[kv.second[i]];
+            a.dst = b.outs[kv.second[i]];
+            a.d = b.images[kv.second[i]];
+            a.eps = b.eps;
+            t->args[i] = a;
+            t->prefix[i] = blocks;
+            blocks += ((p->rows + 1) / 2 + k->xm_lines - 1) / k->xm_lines;
+        }
+        t->prefix[t->nvol] = blocks;
+        b.gx.push_back({k, reinterpret_cast<MultiTable<XArgs> *>(dbase + slot * stride), blocks});
+        ++slot;
+    }
+    for (auto &kv : byy) {
+        auto *t = reinterpret_cast<MultiTable<YArgs> *>(host.data() + slot * stride);
+        const AxisKernels *k = find_axis(kv.first);
+        t->nvol = (int)kv.second.size();
+        int64_t blocks = 0;
+        for (int i = 0; i < t->nvol; ++i) {
+            cubic_rl_plan_s *p = b.plans[kv.second[i]];
+            t->args[i] = y_args(p, p->ws, 0, 0, p->xh);
+            t->prefix[i] = blocks;
+            blocks += (p->xh + k->m_cols - 1) / k->m_cols * p->nz;
+        }
+        t->prefix[t->nvol] = blocks;
+        b.gy.push_back({k, reinterpret_cast<MultiTable<YArgs> *>(dbase + slot * stride), blocks});
+        ++slot;
+    }
+    for (auto &kv : byz) {
+        auto *t = reinterpret_cast<MultiTable<ZArgs> *>(host.data() + slot * stride);
+        const AxisKernels *k = find_axis(kv.first);
+        t->nvol = (int)kv.second.size();
+        int64_t blocks = 0;
+        for (int i = 0; i < t->nvol; ++i) {
+            cubic_rl_plan_s *p = b.plans[kv.second[i]];
+            t->args[i] = z_args(p, p->ws, ZM_CONV, 1.f, 0, p->xh);
+            t->prefix[i] = blocks;
+            blocks += (p->xh + k->m_cols - 1) / k->m_cols * p->ny;
+        }
+        t->prefix[t->nvol] = blocks;
+        b.gz.push_back({k, reinterpret_cast<MultiTable<ZArgs> *>(dbase + slot * stride), blocks});
+        ++slot;
+    }
+    CUBIC_CUDA(cudaMemcpy(b.dmem, host.data(), host.size(), cudaMemcpyHostToDevice));
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_rl_deconvolve_batched(const cubic_rl_plan_t *plans, int n, const float *const *images,
+                                                      int n_iter, float eps, float *const *outs, void *stream)
+{
+    if (!plans || !images || !outs || n < 1 || n > kMaxBatch)
+        return fail(CUBIC_ERR_INVALID_ARG, "plans, images, outs must be non-null and 1 <= n <= %d", kMaxBatch);
+    if (n_iter < 0) return fail(CUBIC_ERR_INVALID_ARG, "n_iter must be >= 0");
+    if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
+    for (int v = 0; v < n; ++v) {
+        if (!plans[v] || !images[v] || !outs[v]) return fail(CUBIC_ERR_INVALID_ARG, "volume %d: null pointer", v);
+        if (!aligned16(images[v]) || !aligned16(outs[v]))
+            return fail(CUBIC_ERR_ALIGNMENT, "volume %d: image and out must be 16-byte aligned", v);
+        if (overlaps(images[v], outs[v], (size_t)plans[v]->V * sizeof(float)))
+            return fail(CUBIC_ERR_INVALID_ARG, "volume %d: out must not overlap image", v);
+        for (int w = 0; w < v; ++w) {
+            if (plans[w] == plans[v]) return fail(CUBIC_ERR_INVALID_ARG, "volumes %d and %d share a plan", w, v);
+            if (overlaps(outs[w], outs[v], std::min(plans[w]->V, plans[v]->V) * sizeof(float)))
+                return fail(CUBIC_ERR_INVALID_ARG, "volumes %d and %d have overlapping outputs", w, v);
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchState *hit = nullptr;
+    for (BatchState *b : g_batches) {
+        if ((int)b->plans.size() != n || b->n_iter != n_iter || b->eps != eps) continue;
+        bool same = true;
+        for (int v = 0; v < n && same; ++v)
+            same = b->plans[v] == plans[v] && b->images[v] == images[v] && b->outs[v] == outs[v];
+        if (same) hit = b;
+    }
+    if (!hit) {
+        for (int v = 0; v < n; ++v) {
+            cubic_status_t s = ensure_workspace(plans[v]);
+            if (s != CUBIC_OK) return s;
+        }
+        BatchState *b = new (std::nothrow) BatchState();
+        if (!b) return fail(CUBIC_ERR_OUT_OF_MEMORY, "host allocation failed");
+        b->plans.assign(plans, plans + n);
+        b->images.assign(images, images + n);
+        b->outs.assign(outs, outs + n);
+        b->n_iter = n_iter;
+        b->eps = eps;
+        cubic_status_t s = build_batch(*b);
+        // capture the sequence on a private stream, then keep the instantiated graph
+        cudaStream_t cap = nullptr;
+        if (s == CUBIC_OK && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+            s = fail(CUBIC_ERR_CUDA, "stream creation failed");
+        if (s == CUBIC_OK) {
+            if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                s = fail(CUBIC_ERR_CUDA, "graph capture failed to start");
+            else {
+                cubic_status_t se = enqueue_batched(*b, cap);
+                cudaError_t ee = cudaStreamEndCapture(cap, &b->graph);
+                if (se != CUBIC_OK) s = se;
+                else if (ee != cudaSuccess) s = fail(CUBIC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ee));
+            }
+        }
+        if (s == CUBIC_OK && cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+            s = fail(CUBIC_ERR_CUDA, "graph instantiation failed");
+        if (s == CUBIC_OK) cudaGraphGetNodes(b->graph, nullptr, &b->kernel_nodes);
+        if (cap) cudaStreamDestroy(cap);
+        if (s != CUBIC_OK) {
+            delete b;
+            return s;
+        }
+        if (g_batches.size() >= 4) {
+            cudaDeviceSynchronize();
+            delete g_batches.front();
+            g_batches.erase(g_batches.begin());
+        }
+        g_batches.push_back(b);
+        hit = b;
+    }
+    g_batch_last_nodes = (int64_t)hit->kernel_nodes;
+    CUBIC_CUDA(cudaGraphLaunch(hit->exec, st));
+    return CUBIC_OK;
+}
+
+extern "C" int64_t cubic_rl_batched_graph_nodes(void)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    return g_batch_last_nodes;
 }
 
 // ------------------------------------------------------------------ allocation-free entry point

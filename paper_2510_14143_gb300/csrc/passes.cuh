@@ -110,7 +110,7 @@ constexpr size_t x_smem_bytes()
 }
 
 template <int N, int P, int L, int MODE>
-__global__ void __launch_bounds__(P * L) k_xpass(XArgs a)
+__device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
 {
     constexpr int E = N / P;
     constexpr bool kTma = x_uses_tma<N, MODE>();
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(P * L) k_xpass(XArgs a)
 
     const int t = threadIdx.x % P;
     const int l = threadIdx.x / P;
-    const int64_t m = (int64_t)blockIdx.x * L + l;
+    const int64_t m = block * L + l;
     const int64_t r0 = 2 * m, r1 = 2 * m + 1;
     const bool ok0 = r0 < a.rows, ok1 = r1 < a.rows;
     SmemPadded sm{xch + l * x_smem_line<N>()};
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(P * L) k_xpass(XArgs a)
         __syncthreads();
         if (threadIdx.x == 0) {
             // this CTA's rows are contiguous: one copy
-            const int64_t row0 = (int64_t)blockIdx.x * L * 2;
+            const int64_t row0 = block * L * 2;
             const int64_t left = a.rows - row0;
             const int64_t nrows = left < 2 * L ? left : 2 * L;
             const float *src = (MODE == XM_RATIO ? a.d : a.u) + row0 * N;
@@ -247,18 +247,57 @@ __global__ void __launch_bounds__(P * L) k_xpass(XArgs a)
     }
 }
 
+// ------------------------------------------------------------------ multi-volume launches
+// One launch covers several volumes of the same axis length (the batched path):
+// block b belongs to the volume v with prefix[v] <= b < prefix[v+1].
+
+constexpr int kMaxBatch = 256;
+
+template <class Args>
+struct MultiTable {
+    int nvol;
+    int64_t prefix[kMaxBatch + 1];
+    Args args[kMaxBatch];
+};
+
+__device__ __forceinline__ int find_volume(const int64_t *prefix, int nvol, int64_t b)
+{
+    int lo = 0, hi = nvol - 1;
+    while (lo < hi) {  // largest v with prefix[v] <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// tab == nullptr: one volume, arguments by value.  Otherwise the volumes of tab.
+template <int N, int P, int L, int MODE>
+__global__ void __launch_bounds__(P * L) k_xpass(XArgs a, const MultiTable<XArgs> *tab)
+{
+    int64_t block = blockIdx.x;
+    if (tab) {
+        const int v = find_volume(tab->prefix, tab->nvol, blockIdx.x);
+        a = tab->args[v];
+        block -= tab->prefix[v];
+    }
+    x_body<N, P, L, MODE>(a, block);
+}
+
 // ------------------------------------------------------------------ Y pass
 
 template <int N, int P, int B>
-__global__ void __launch_bounds__(P * B) k_ypass(YArgs a)
+__device__ __forceinline__ void y_body(const YArgs &a, const int64_t bx, const int64_t by)
 {
     constexpr int E = N / P;
     extern __shared__ float2 smem_y[];
     const int b = threadIdx.x % B;
     const int t = threadIdx.x / B;
-    const int64_t col = a.col0 + (int64_t)blockIdx.x * B + b;
+    const int64_t col = a.col0 + bx * B + b;
     const bool ok = col < a.col1;
-    float2 *base = a.spec + (int64_t)blockIdx.y * N * a.xp + col;
+    float2 *base = a.spec + by * N * a.xp + col;
     SmemStrided sm{smem_y + b, B};
     auto sync = [] { __syncthreads(); };
     float2 v[E];
@@ -277,19 +316,38 @@ __global__ void __launch_bounds__(P * B) k_ypass(YArgs a)
     }
 }
 
+// tab == nullptr: one volume, grid (column tiles, nz).  Otherwise a 1D grid over the
+// volumes of tab, volume v's blocks flattened as tile + ntiles * z; `inverse` then
+// overrides the table's direction.
+template <int N, int P, int B>
+__global__ void __launch_bounds__(P * B) k_ypass(YArgs a, const MultiTable<YArgs> *tab, int inverse)
+{
+    int64_t bx = blockIdx.x, by = blockIdx.y;
+    if (tab) {
+        const int v = find_volume(tab->prefix, tab->nvol, blockIdx.x);
+        a = tab->args[v];
+        a.inverse = inverse;
+        const int64_t local = (int64_t)blockIdx.x - tab->prefix[v];
+        const int64_t nct = (a.col1 - a.col0 + B - 1) / B;
+        bx = local % nct;
+        by = local / nct;
+    }
+    y_body<N, P, B>(a, bx, by);
+}
+
 // ------------------------------------------------------------------ Z pass
 
 template <int N, int P, int B>
-__global__ void __launch_bounds__(P * B) k_zpass(ZArgs a)
+__device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const int64_t by)
 {
     constexpr int E = N / P;
     extern __shared__ float2 smem_z[];
     const int b = threadIdx.x % B;
     const int t = threadIdx.x / B;
-    const int64_t col = a.col0 + (int64_t)blockIdx.x * B + b;
+    const int64_t col = a.col0 + bx * B + b;
     const bool ok = col < a.col1;
     const int64_t zstride = a.ny * a.xp;
-    const int64_t off = (int64_t)blockIdx.y * a.xp + col;
+    const int64_t off = by * a.xp + col;
     float2 *base = a.spec + off;
     SmemStrided sm{smem_z + b, B};
     auto sync = [] { __syncthreads(); };
@@ -329,6 +387,24 @@ __global__ void __launch_bounds__(P * B) k_zpass(ZArgs a)
             base[(int64_t)(t + P * i) * zstride] = cconj(v[i]);
         });
     }
+}
+
+// as k_ypass: tab == nullptr for one volume (grid: column tiles, ny), else volume v's
+// blocks flattened as tile + ntiles * y, with `mode` overriding the table's mode.
+template <int N, int P, int B>
+__global__ void __launch_bounds__(P * B) k_zpass(ZArgs a, const MultiTable<ZArgs> *tab, int mode)
+{
+    int64_t bx = blockIdx.x, by = blockIdx.y;
+    if (tab) {
+        const int v = find_volume(tab->prefix, tab->nvol, blockIdx.x);
+        a = tab->args[v];
+        a.mode = mode;
+        const int64_t local = (int64_t)blockIdx.x - tab->prefix[v];
+        const int64_t nct = (a.col1 - a.col0 + B - 1) / B;
+        bx = local % nct;
+        by = local / nct;
+    }
+    z_body<N, P, B>(a, bx, by);
 }
 
 }  // namespace cubic

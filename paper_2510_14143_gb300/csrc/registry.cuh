@@ -21,6 +21,9 @@ namespace cubic {
 using XLaunch = cudaError_t (*)(const XArgs &, cudaStream_t);
 using YLaunch = cudaError_t (*)(const YArgs &, cudaStream_t);
 using ZLaunch = cudaError_t (*)(const ZArgs &, cudaStream_t);
+using XMultiLaunch = cudaError_t (*)(const MultiTable<XArgs> *, int64_t blocks, cudaStream_t);
+using YMultiLaunch = cudaError_t (*)(const MultiTable<YArgs> *, int64_t blocks, int inverse, cudaStream_t);
+using ZMultiLaunch = cudaError_t (*)(const MultiTable<ZArgs> *, int64_t blocks, int mode, cudaStream_t);
 
 constexpr int kMaxVariants = 6;
 
@@ -41,6 +44,12 @@ struct AxisKernels {
     int nx = 0, nyz = 0;  // number of X and Y/Z variants
     XVariant xv[kMaxVariants];
     YZVariant yzv[kMaxVariants];
+    // multi-volume launches (batched path): X with xv[0]'s shape, Y/Z with P0 x 16 columns
+    XMultiLaunch xm[XM_COUNT] = {};
+    YMultiLaunch ym = nullptr;
+    ZMultiLaunch zm = nullptr;
+    int xm_lines = 0;  // line pairs per X CTA
+    int m_cols = 16;   // columns per Y/Z CTA
 };
 
 // Table lookup; nullptr if n has no kernels.
@@ -64,7 +73,7 @@ cudaError_t launch_x(const XArgs &a, cudaStream_t st)
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (grid == 0) return cudaSuccess;
-    fn<<<(unsigned)grid, P * L, smem, st>>>(a);
+    fn<<<(unsigned)grid, P * L, smem, st>>>(a, nullptr);
     return cudaGetLastError();
 }
 
@@ -77,7 +86,7 @@ cudaError_t launch_y(const YArgs &a, cudaStream_t st)
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    fn<<<grid, P * B, smem, st>>>(a);
+    fn<<<grid, P * B, smem, st>>>(a, nullptr, a.inverse);
     return cudaGetLastError();
 }
 
@@ -89,7 +98,8 @@ cudaError_t launch_z(const ZArgs &a, cudaStream_t st)
     auto fn = k_zpass<N, P, B>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
-    fn<<<grid, P * B, smem, st>>>(a);
+    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+    fn<<<grid, P * B, smem, st>>>(a, nullptr, a.mode);
     return cudaGetLastError();
 }
 
@@ -204,6 +214,42 @@ constexpr int tma_cols()
     return col_smem_bytes<N, 16, KIND>() <= 200 * 1024 ? 16 : col_smem_bytes<N, 8, KIND>() <= 200 * 1024 ? 8 : 0;
 }
 
+template <int N, int P, int L, int MODE>
+cudaError_t launch_x_multi(const MultiTable<XArgs> *tab, int64_t blocks, cudaStream_t st)
+{
+    constexpr size_t smem = x_smem_bytes<N, L, MODE>();
+    auto fn = k_xpass<N, P, L, MODE>;
+    static cudaError_t attr = set_smem((const void *)fn, smem);
+    if (attr != cudaSuccess) return attr;
+    if (blocks == 0) return cudaSuccess;
+    fn<<<(unsigned)blocks, P * L, smem, st>>>(XArgs{}, tab);
+    return cudaGetLastError();
+}
+
+template <int N, int P, int B>
+cudaError_t launch_y_multi(const MultiTable<YArgs> *tab, int64_t blocks, int inverse, cudaStream_t st)
+{
+    constexpr size_t smem = sizeof(float2) * B * N;
+    auto fn = k_ypass<N, P, B>;
+    static cudaError_t attr = set_smem((const void *)fn, smem);
+    if (attr != cudaSuccess) return attr;
+    if (blocks == 0) return cudaSuccess;
+    fn<<<(unsigned)blocks, P * B, smem, st>>>(YArgs{}, tab, inverse);
+    return cudaGetLastError();
+}
+
+template <int N, int P, int B>
+cudaError_t launch_z_multi(const MultiTable<ZArgs> *tab, int64_t blocks, int mode, cudaStream_t st)
+{
+    constexpr size_t smem = sizeof(float2) * B * N;
+    auto fn = k_zpass<N, P, B>;
+    static cudaError_t attr = set_smem((const void *)fn, smem);
+    if (attr != cudaSuccess) return attr;
+    if (blocks == 0) return cudaSuccess;
+    fn<<<(unsigned)blocks, P * B, smem, st>>>(ZArgs{}, tab, mode);
+    return cudaGetLastError();
+}
+
 template <int N, int P, int L>
 XVariant make_xvariant()
 {
@@ -254,6 +300,16 @@ AxisKernels make_axis()
     constexpr int P0 = S::P0;
     k.xv[0] = make_xvariant<N, P0, S::lines(P0, 128)>();
     k.nx = 1;
+    constexpr int XL = S::lines(P0, 128);
+    k.xm[XM_FWD] = launch_x_multi<N, P0, XL, XM_FWD>;
+    k.xm[XM_INV] = launch_x_multi<N, P0, XL, XM_INV>;
+    k.xm[XM_RATIO] = launch_x_multi<N, P0, XL, XM_RATIO>;
+    k.xm[XM_UPDATE] = launch_x_multi<N, P0, XL, XM_UPDATE>;
+    k.xm[XM_FINAL] = launch_x_multi<N, P0, XL, XM_FINAL>;
+    k.xm_lines = XL;
+    k.ym = launch_y_multi<N, P0, 16>;
+    k.zm = launch_z_multi<N, P0, 16>;
+    k.m_cols = 16;
     k.nyz = 0;
     constexpr int BY = tma_cols<N, COL_Y>(), BZ = tma_cols<N, COL_Z>();
     if constexpr (S::kTuned && (BY > 0 || BZ > 0)) {

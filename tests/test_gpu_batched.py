@@ -1,0 +1,114 @@
+"""Batched deconvolution (many uneven volumes, one CUDA graph) against the plain path and the oracle.
+
+The batched path runs the same per-length transforms as the plain path; with the
+default launch shapes (same threads per line, hence the same radix plan) the results
+are bitwise equal, and they match the FP64 oracle within the plain path's tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_14143_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cr():
+    from paper_2510_14143_gb300 import build
+    build.build()
+    import paper_2510_14143_gb300 as m
+    return m
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def make_batch(cr, shapes, seed0=0):
+    vols, plans, imgs = [], [], []
+    for j, shape in enumerate(shapes):
+        d, _ = synth.make_volume(shape, max(1, int(np.prod(shape)) // 20000), (1.5, 3.0), 10.0, 1.5, 3.0,
+                                 5000 + seed0 + j)
+        psf = torch.empty(shape, dtype=torch.float32, device="cuda")
+        cr.cubic_psf_gaussian(shape, 1.5, 3.0, 1.0, psf)
+        plan = cr.cubic_rl_plan(shape, psf)
+        cr.cubic_rl_plan_set_variants(plan, 0, 0, 0)
+        vols.append((d, psf))
+        plans.append(plan)
+        imgs.append(torch.from_numpy(d).cuda())
+    return vols, plans, imgs
+
+
+SHAPES = [(48, 50, 54), (60, 64, 72), (75, 80, 81), (81, 75, 90), (100, 96, 108), (50, 125, 48),
+          (5, 9, 15), (64, 64, 64), (1, 16, 24), (60, 64, 72)]
+
+
+def test_batched_equals_plain_calls(cr):
+    vols, plans, imgs = make_batch(cr, SHAPES)
+    n_iter = 7
+    outs = [torch.empty_like(i) for i in imgs]
+    cr.cubic_rl_deconvolve_batched(plans, imgs, n_iter, 1e-6, outs)
+    torch.cuda.synchronize()
+    assert cr.cubic_rl_batched_graph_nodes() > 0
+    for plan, img, out in zip(plans, imgs, outs):
+        ref = torch.empty_like(img)
+        cr.cubic_rl_deconvolve(plan, img, n_iter, 1e-6, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+
+
+def test_batched_matches_oracle_and_replays(cr):
+    shapes = [(48, 60, 75), (81, 50, 64), (54, 72, 100)]
+    vols, plans, imgs = make_batch(cr, shapes, seed0=100)
+    outs = [torch.empty_like(i) for i in imgs]
+    n_iter = 12
+    cr.cubic_rl_deconvolve_batched(plans, imgs, n_iter, 1e-6, outs)
+    torch.cuda.synchronize()
+    first = [o.clone() for o in outs]
+    for (d, psf), out in zip(vols, outs):
+        ref = oracle.rl(d, psf.cpu().numpy(), n_iter, 1e-6)
+        assert rel_l2(out.cpu().numpy(), ref) <= 1e-4
+    for o in outs:
+        o.fill_(float("nan"))
+    cr.cubic_rl_deconvolve_batched(plans, imgs, n_iter, 1e-6, outs)   # graph replay
+    torch.cuda.synchronize()
+    for a, b in zip(first, outs):
+        assert torch.equal(a, b)
+
+
+def test_batched_workload_sample(cr):
+    # the 64-volume workload's first volumes (its sizes and generator), 50 iterations, vs the oracle
+    shapes = synth.batch_shapes()[:3]
+    plans, imgs, vols = [], [], []
+    for j, shape in enumerate(shapes):
+        d, _ = synth.batch_volume(j, shape)
+        psf = torch.empty(shape, dtype=torch.float32, device="cuda")
+        cr.cubic_psf_gaussian(shape, synth.SMALL.psf_sigma_xy, synth.SMALL.psf_sigma_z, 1.0, psf)
+        plans.append(cr.cubic_rl_plan(shape, psf))
+        imgs.append(torch.from_numpy(d).cuda())
+        vols.append((d, psf.cpu().numpy()))
+    outs = [torch.empty_like(i) for i in imgs]
+    cr.cubic_rl_deconvolve_batched(plans, imgs, synth.BATCH_ITERS, 1e-6, outs)
+    torch.cuda.synchronize()
+    for (d, psf), out in zip(vols, outs):
+        ref = oracle.rl(d, psf, synth.BATCH_ITERS, 1e-6)
+        assert rel_l2(out.cpu().numpy(), ref) <= 1e-4
+
+
+def test_batched_errors(cr):
+    vols, plans, imgs = make_batch(cr, [(8, 8, 8), (8, 12, 10)])
+    outs = [torch.empty_like(i) for i in imgs]
+    with pytest.raises(cr.CubicError) as e:
+        cr.cubic_rl_deconvolve_batched([plans[0], plans[0]], [imgs[0], imgs[0]], 2, 1e-6,
+                                       [outs[0], torch.empty_like(outs[0])])
+    assert e.value.status == 1
+    with pytest.raises(cr.CubicError) as e:
+        cr.cubic_rl_deconvolve_batched(plans, imgs, 2, 1e-6, [imgs[0], outs[1]])   # out aliases image
+    assert e.value.status == 1
+    with pytest.raises(cr.CubicError) as e:
+        cr.cubic_rl_deconvolve_batched(plans, imgs, 2, -1.0, outs)
+    assert e.value.status == 1
