@@ -183,6 +183,42 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve_noalloc(const int64_t dims[3], cons
                                                      const float *image, int n_iter, float eps,
                                                      float *out, void *stream);
 
+/* ---- differentiation (reverse mode through the iterations) ---- */
+
+/* cubic_rl_deconvolve that also stores the estimate u_k at every k = 0, ckpt_every,
+ * 2*ckpt_every, ... < n_iter into ckpts (device float32, ceil(n_iter/ckpt_every) volumes,
+ * back to back) for cubic_rl_backward.  n_iter >= 1, ckpt_every >= 1; image, out and
+ * ckpts must not overlap. */
+CUBIC_API cubic_status_t cubic_rl_deconvolve_ckpt(cubic_rl_plan_t plan, const float *image, int n_iter,
+                                                  float eps, int ckpt_every, float *ckpts, float *out,
+                                                  void *stream);
+
+/* Device scratch the backward keeps in the plan for this checkpoint spacing:
+ * (4*ckpt_every + 5) volumes of floats plus three half spectra. */
+CUBIC_API cubic_status_t cubic_rl_backward_workspace_bytes(cubic_rl_plan_t plan, int ckpt_every,
+                                                           size_t *bytes);
+
+/* Gradient of a loss L(u_{n_iter}) through the n_iter iterations of the paper's RL step
+ * (Section 4: forward convolution, ratio, flipped-PSF convolution, multiplicative
+ * update), given grad_out = dL/du_{n_iter} (device float32 volume) and the checkpoints
+ * of cubic_rl_deconvolve_ckpt for the same (plan, image, n_iter, eps, ckpt_every).
+ * Writes grad_image = dL/dimage (through every ratio and through u0 = max(mean, eps));
+ * grad_psf = dL/dpsf for the centred PSF (added to grad_psf when accumulate_psf != 0).
+ * Either output may be NULL.  The derivative of max(b, eps) is taken as 1 where
+ * b > eps, else 0.  Segments between checkpoints are recomputed; their iterates live in
+ * plan-owned scratch (allocated on first use; cubic_rl_backward_workspace_bytes). */
+CUBIC_API cubic_status_t cubic_rl_backward(cubic_rl_plan_t plan, const float *image, int n_iter, float eps,
+                                           int ckpt_every, const float *ckpts, const float *grad_out,
+                                           float *grad_image, float *grad_psf, int accumulate_psf,
+                                           void *stream);
+
+/* dL/d(sigma_xy, sigma_z, amp) of the Gaussian PSF of cubic_psf_gaussian given
+ * grad_psf = dL/dpsf: writes three floats to grad_params (device memory).  The PSF's flux
+ * sum is in double, the other five reductions in compensated float32. */
+CUBIC_API cubic_status_t cubic_psf_gaussian_backward(const int64_t dims[3], float sigma_xy, float sigma_z,
+                                                     float amp, const float *grad_psf, float *grad_params,
+                                                     void *stream);
+
 /* ---- launch accounting and per-kernel timing ---- */
 
 /* Number of kernel kinds and the name of each (static strings). */

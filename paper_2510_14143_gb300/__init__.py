@@ -62,6 +62,10 @@ _SIGS = {
     "cubic_rl_deconvolve_batched": ([ctypes.POINTER(_vp), _ci, ctypes.POINTER(_vp), _ci, _cf, ctypes.POINTER(_vp),
                                      _vp], _ci),
     "cubic_rl_batched_graph_nodes": ([], _i64),
+    "cubic_rl_deconvolve_ckpt": ([_vp, _vp, _ci, _cf, _ci, _vp, _vp, _vp], _ci),
+    "cubic_rl_backward_workspace_bytes": ([_vp, _ci, ctypes.POINTER(_sz)], _ci),
+    "cubic_rl_backward": ([_vp, _vp, _ci, _cf, _ci, _vp, _vp, _vp, _vp, _ci, _vp], _ci),
+    "cubic_psf_gaussian_backward": ([ctypes.POINTER(_i64), _cf, _cf, _cf, _vp, _vp, _vp], _ci),
     "cubic_rl_kernel_kinds": ([], _ci),
     "cubic_rl_kernel_name": ([_ci], ctypes.c_char_p),
     "cubic_rl_profile": ([_vp, _ci, _ci], _ci),
@@ -284,6 +288,53 @@ def cubic_rl_deconvolve_batched(plans, images, n_iter: int, eps: float, outs, st
 
 def cubic_rl_batched_graph_nodes() -> int:
     return int(lib().cubic_rl_batched_graph_nodes())
+
+
+def n_checkpoints(n_iter: int, ckpt_every: int) -> int:
+    return (int(n_iter) + int(ckpt_every) - 1) // int(ckpt_every)
+
+
+def cubic_rl_deconvolve_ckpt(plan: Plan, image, n_iter: int, eps: float, ckpt_every: int, ckpts, out,
+                             stream=None) -> None:
+    import torch
+    _check(lib().cubic_rl_deconvolve_ckpt(plan.handle, _ptr(image, torch.float32, plan.voxels, "image"), int(n_iter),
+                                          float(eps), int(ckpt_every),
+                                          _ptr(ckpts, torch.float32, plan.voxels * n_checkpoints(n_iter, ckpt_every),
+                                               "ckpts"),
+                                          _ptr(out, torch.float32, plan.voxels, "out"), _stream(stream)),
+           "cubic_rl_deconvolve_ckpt")
+
+
+def cubic_rl_backward_workspace_bytes(plan: Plan, ckpt_every: int) -> int:
+    n = _sz()
+    _check(lib().cubic_rl_backward_workspace_bytes(plan.handle, int(ckpt_every), ctypes.byref(n)),
+           "cubic_rl_backward_workspace_bytes")
+    return int(n.value)
+
+
+def cubic_rl_backward(plan: Plan, image, n_iter: int, eps: float, ckpt_every: int, ckpts, grad_out,
+                      grad_image=None, grad_psf=None, accumulate_psf: bool = False, stream=None) -> None:
+    import torch
+    v = plan.voxels
+    _check(lib().cubic_rl_backward(plan.handle, _ptr(image, torch.float32, v, "image"), int(n_iter), float(eps),
+                                   int(ckpt_every),
+                                   _ptr(ckpts, torch.float32, v * n_checkpoints(n_iter, ckpt_every), "ckpts"),
+                                   _ptr(grad_out, torch.float32, v, "grad_out"),
+                                   None if grad_image is None else _ptr(grad_image, torch.float32, v, "grad_image"),
+                                   None if grad_psf is None else _ptr(grad_psf, torch.float32, v, "grad_psf"),
+                                   int(bool(accumulate_psf)), _stream(stream)), "cubic_rl_backward")
+
+
+def cubic_psf_gaussian_backward(dims, sigma_xy: float, sigma_z: float, amp: float, grad_psf, grad_params,
+                                stream=None) -> None:
+    """grad_params: float32 CUDA tensor of 3 elements <- dL/d(sigma_xy, sigma_z, amp)."""
+    import torch
+    dims = tuple(int(d) for d in dims)
+    d = (_i64 * 3)(*dims)
+    _check(lib().cubic_psf_gaussian_backward(d, float(sigma_xy), float(sigma_z), float(amp),
+                                             _ptr(grad_psf, torch.float32, dims[0] * dims[1] * dims[2], "grad_psf"),
+                                             _ptr(grad_params, torch.float32, 3, "grad_params"), _stream(stream)),
+           "cubic_psf_gaussian_backward")
 
 
 def cubic_rl_kernel_kinds() -> int:

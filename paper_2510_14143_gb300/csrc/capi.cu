@@ -212,6 +212,8 @@ struct cubic_rl_plan_s {
     float2 *ws = nullptr;       // spectrum work array
     bool own_ws = false;
     float *stage_in = nullptr, *stage_out = nullptr;  // device copies for host-buffer calls, owned
+    unsigned char *bwd = nullptr;                      // gradient scratch, owned
+    size_t bwd_bytes = 0;
     // launch accounting and optional per-kernel CUDA-event timing
     int64_t launches[KK_COUNT] = {};
     double bytes[KK_COUNT] = {};
@@ -504,6 +506,7 @@ extern "C" cubic_status_t cubic_rl_plan_destroy(cubic_rl_plan_t plan)
     if (plan->own_ws) cudaFree(plan->ws);
     cudaFree(plan->stage_in);
     cudaFree(plan->stage_out);
+    cudaFree(plan->bwd);
     for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
     delete plan;
     return CUBIC_OK;
@@ -535,6 +538,13 @@ static bool overlaps(const void *a, const void *b, size_t n)
 {
     const char *x = (const char *)a, *y = (const char *)b;
     return x < y + n && y < x + n;
+}
+
+// [a, a + na) and [b, b + nb) share a byte
+static bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + nb && y < x + na;
 }
 
 // u0 = max(mean(image), eps) into out.
@@ -946,6 +956,426 @@ extern "C" cubic_status_t cubic_rl_stream_status(cubic_rl_plan_t plan, void *str
         CUBIC_CUDA(cudaMemsetAsync(plan->err, 0, sizeof(unsigned), st));
         return fail(CUBIC_ERR_TIMEOUT, "a device wait timed out (error word 0x%x)", word);
     }
+    return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ differentiation
+//
+// Reverse mode through n_iter Richardson-Lucy iterations.  One iteration,
+//   b = h * u,  c = max(b, eps),  r = d / c,  q = h (x) r,  u' = u q,
+// has the adjoint (g = dL/du'):
+//   qbar = g u;  ubar = g q + h (x) bbar;  rbar = h * qbar;
+//   dbar += rbar / c;  bbar = -rbar d / c^2 [b > eps];
+//   dL/dh0 += bbar (x) u + r (x) qbar  ->  spectrum  G += Bbar conj(U) + conj(Qbar) R,
+// where * is the circular convolution and (x) the correlation (convolution with the
+// flipped PSF).  The forward stores u every `ckpt_every` iterations; the backward
+// recomputes each segment from its checkpoint, keeping u, b, r and q of every
+// iteration of the segment, then walks the segment backwards.
+
+__global__ void k_adj_q(const float *__restrict__ g, const float *__restrict__ u, const float *__restrict__ q,
+                        float *__restrict__ qbar, float *__restrict__ ubar, int64_t V)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        qbar[i] = gi * u[i];
+        ubar[i] = gi * q[i];
+    }
+}
+
+// in: rbar (in bbar's buffer); out: bbar; dbar += rbar / c
+__global__ void k_adj_r(const float *__restrict__ b, const float *__restrict__ d, float *__restrict__ rb,
+                        float *__restrict__ dbar, float eps, int64_t V)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        const float bi = b[i];
+        const float c = fmaxf(bi, eps);
+        const float r = rb[i];
+        dbar[i] += r / c;
+        rb[i] = bi > eps ? -r * d[i] / (c * c) : 0.f;
+    }
+}
+
+__global__ void k_add(float *__restrict__ a, const float *__restrict__ b, int64_t V)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] += b[i];
+}
+
+// dbar += sum(g) / V where mean(d) > eps (u0 = max(mean(d), eps))
+__global__ void k_add_mean_grad(float *__restrict__ dbar, const double *__restrict__ sum_g,
+                                const double *__restrict__ sum_d, int64_t V, float eps)
+{
+    const bool pass = sum_d[0] / (double)V > (double)eps;
+    const float add = pass ? (float)(sum_g[0] / (double)V) : 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x)
+        dbar[i] += add;
+}
+
+// Half-spectrum pointwise kernels over [rows][xp] (columns < xh):
+//   mode 0: s *= H        mode 1: s *= conj(H)
+__global__ void k_spec_mul(float2 *__restrict__ s, const float2 *__restrict__ H, int64_t rows, int64_t xh,
+                           int64_t xp, int mode)
+{
+    const int64_t n = rows * xh;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = (i / xh) * xp + i % xh;
+        s[o] = mode ? cmulconj(s[o], H[o]) : cmul(s[o], H[o]);
+    }
+}
+
+//   mode 0: G += conj(A) B     mode 1: G += A conj(B)
+__global__ void k_spec_acc(float2 *__restrict__ G, const float2 *__restrict__ A, const float2 *__restrict__ B,
+                           int64_t rows, int64_t xh, int64_t xp, int mode)
+{
+    const int64_t n = rows * xh;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = (i / xh) * xp + i % xh;
+        const float2 p = mode ? cmulconj(A[o], B[o]) : cmulconj(B[o], A[o]);
+        G[o] = cadd(G[o], p);
+    }
+}
+
+// p(x) = h0(x - floor(n/2)) (+= p when accumulate): PSF gradient back to centred indexing
+__global__ void k_origin_to_center(const float *__restrict__ h0, float *__restrict__ p, int64_t nz, int64_t ny,
+                                   int64_t nx, int accumulate)
+{
+    const int64_t V = nz * ny * nx;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+        int64_t xs = x + nx / 2, ys = y + ny / 2, zs = z + nz / 2;
+        if (xs >= nx) xs -= nx;
+        if (ys >= ny) ys -= ny;
+        if (zs >= nz) zs -= nz;
+        const int64_t j = (zs * ny + ys) * nx + xs;
+        p[j] = accumulate ? p[j] + h0[i] : h0[i];
+    }
+}
+
+// Unnormalised (scale = 1) or normalised (scale = 1/V) inverse 3D transform of a half spectrum.
+static cubic_status_t enqueue_inverse3(cubic_rl_plan_s *p, float2 *spec, float *out, float scale, cudaStream_t st)
+{
+    CUBIC_CUDA(run_z(p, z_args(p, spec, ZM_INV_SCALE, scale, 0, p->xh), st));
+    CUBIC_CUDA(run_y(p, y_args(p, spec, 1, 0, p->xh), st));
+    XArgs xa = x_args(p);
+    xa.spec_in = spec;
+    xa.dst = out;
+    CUBIC_CUDA(run_x(p, XM_INV, xa, st));
+    return CUBIC_OK;
+}
+
+// Recompute iterations k0 .. k0+cnt-1 from u_k0 = seg_u[0], keeping u, b, r, q per iteration.
+static cubic_status_t enqueue_segment(cubic_rl_plan_s *p, const float *image, float eps, int cnt, float *const *seg_u,
+                                      float *const *seg_b, float *const *seg_r, float *const *seg_q, float2 *spec,
+                                      cudaStream_t st)
+{
+    XArgs xa = x_args(p);
+    xa.spec_in = spec;
+    xa.spec_out = spec;
+    xa.src = seg_u[0];
+    xa.d = image;
+    xa.eps = eps;
+    CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
+    cubic_status_t s;
+    for (int j = 0; j < cnt; ++j) {
+        if ((s = enqueue_yzy(p, spec, ZM_CONV, st)) != CUBIC_OK) return s;
+        xa.keep_a = seg_b[j];
+        xa.keep_b = seg_r[j];
+        CUBIC_CUDA(run_x(p, XM_RATIO, xa, st));
+        if ((s = enqueue_yzy(p, spec, ZM_CORR, st)) != CUBIC_OK) return s;
+        xa.keep_a = seg_q[j];
+        xa.keep_b = nullptr;
+        xa.u = seg_u[j];
+        xa.dst = seg_u[j + 1];
+        CUBIC_CUDA(run_x(p, j + 1 < cnt ? XM_UPDATE : XM_FINAL, xa, st));
+        xa.keep_a = nullptr;
+    }
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_rl_deconvolve_ckpt(cubic_rl_plan_t plan, const float *image, int n_iter, float eps,
+                                                   int ckpt_every, float *ckpts, float *out, void *stream)
+{
+    if (!plan || !image || !out || !ckpts) return fail(CUBIC_ERR_INVALID_ARG, "null pointer");
+    if (n_iter < 1 || ckpt_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "n_iter and ckpt_every must be >= 1");
+    if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
+    if (!aligned16(image) || !aligned16(out) || !aligned16(ckpts))
+        return fail(CUBIC_ERR_ALIGNMENT, "image, out and ckpts must be 16-byte aligned");
+    const size_t vb = (size_t)plan->V * sizeof(float);
+    const int nck = (n_iter + ckpt_every - 1) / ckpt_every;
+    if (overlaps(image, out, vb) || ranges_overlap(image, vb, ckpts, vb * nck) || ranges_overlap(out, vb, ckpts, vb * nck))
+        return fail(CUBIC_ERR_INVALID_ARG, "image, out and ckpts must not overlap");
+    cubic_status_t s = ensure_workspace(plan);
+    if (s != CUBIC_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    cubic_rl_plan_s *p = plan;
+    if ((s = enqueue_init(p, image, eps, out, st)) != CUBIC_OK) return s;
+    XArgs xa = x_args(p);
+    xa.spec_in = p->ws;
+    xa.spec_out = p->ws;
+    xa.src = out;
+    xa.u = out;
+    xa.dst = out;
+    xa.d = image;
+    xa.eps = eps;
+    CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
+    for (int k = 0; k < n_iter; ++k) {
+        if (k % ckpt_every == 0)
+            CUBIC_CUDA(cudaMemcpyAsync(ckpts + (size_t)(k / ckpt_every) * p->V, out, vb, cudaMemcpyDeviceToDevice, st));
+        if ((s = enqueue_yzy(p, p->ws, ZM_CONV, st)) != CUBIC_OK) return s;
+        CUBIC_CUDA(run_x(p, XM_RATIO, xa, st));
+        if ((s = enqueue_yzy(p, p->ws, ZM_CORR, st)) != CUBIC_OK) return s;
+        CUBIC_CUDA(run_x(p, k + 1 < n_iter ? XM_UPDATE : XM_FINAL, xa, st));
+    }
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_rl_backward_workspace_bytes(cubic_rl_plan_t plan, int ckpt_every, size_t *bytes)
+{
+    if (!plan || !bytes || ckpt_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "bad arguments");
+    const size_t vb = ((size_t)plan->V * sizeof(float) + 255) / 256 * 256;
+    const size_t sb = (spec_elems(plan) * sizeof(float2) + 255) / 256 * 256;
+    const size_t rb = ((kReduceBlocks + 1) * sizeof(double) + 255) / 256 * 256;
+    *bytes = vb * (4 * (size_t)ckpt_every + 1 + 4) + 3 * sb + rb;
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_rl_backward(cubic_rl_plan_t plan, const float *image, int n_iter, float eps,
+                                            int ckpt_every, const float *ckpts, const float *grad_out,
+                                            float *grad_image, float *grad_psf, int accumulate_psf, void *stream)
+{
+    if (!plan || !image || !ckpts || !grad_out) return fail(CUBIC_ERR_INVALID_ARG, "null pointer");
+    if (n_iter < 1 || ckpt_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "n_iter and ckpt_every must be >= 1");
+    if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
+    if (!aligned16(image) || !aligned16(ckpts) || !aligned16(grad_out) || (grad_image && !aligned16(grad_image)) ||
+        (grad_psf && !aligned16(grad_psf)))
+        return fail(CUBIC_ERR_ALIGNMENT, "pointers must be 16-byte aligned");
+    cubic_rl_plan_s *p = plan;
+    cubic_status_t s = ensure_workspace(p);
+    if (s != CUBIC_OK) return s;
+    size_t need = 0;
+    cubic_rl_backward_workspace_bytes(p, ckpt_every, &need);
+    if (p->bwd_bytes < need) {
+        cudaDeviceSynchronize();
+        cudaFree(p->bwd);
+        p->bwd = nullptr;
+        p->bwd_bytes = 0;
+        void *m = nullptr;
+        CUBIC_CUDA(cudaMalloc(&m, need));
+        p->bwd = (unsigned char *)m;
+        p->bwd_bytes = need;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t V = p->V;
+    const size_t vb = ((size_t)V * sizeof(float) + 255) / 256 * 256;
+    const size_t sb = (spec_elems(p) * sizeof(float2) + 255) / 256 * 256;
+    unsigned char *m = p->bwd;
+    const int c = ckpt_every;
+    std::vector<float *> seg_u(c + 1), seg_b(c), seg_r(c), seg_q(c);
+    for (int j = 0; j <= c; ++j) seg_u[j] = (float *)(m + vb * j);
+    for (int j = 0; j < c; ++j) {
+        seg_b[j] = (float *)(m + vb * (c + 1 + j));
+        seg_r[j] = (float *)(m + vb * (2 * c + 1 + j));
+        seg_q[j] = (float *)(m + vb * (3 * c + 1 + j));
+    }
+    float *g = (float *)(m + vb * (4 * c + 1));     // dL/du of the current iteration
+    float *ubar = (float *)(m + vb * (4 * c + 2));
+    float *tmp = (float *)(m + vb * (4 * c + 3));   // qbar, then rbar / bbar
+    float *dbar = (float *)(m + vb * (4 * c + 4));
+    float2 *S1 = (float2 *)(m + vb * (4 * c + 5));
+    float2 *S2 = (float2 *)((unsigned char *)S1 + sb);
+    float2 *G = (float2 *)((unsigned char *)S2 + sb);
+    double *red = (double *)((unsigned char *)G + sb);  // kReduceBlocks + 1 doubles
+    float2 *spec = p->ws;
+    const unsigned gr = grid_for(V, 256);
+    const int64_t rows = p->rows;
+    const unsigned gs = grid_for(rows * p->xh, 256);
+
+    CUBIC_CUDA(cudaMemcpyAsync(g, grad_out, (size_t)V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    CUBIC_CUDA(cudaMemsetAsync(dbar, 0, (size_t)V * sizeof(float), st));
+    CUBIC_CUDA(cudaMemsetAsync(G, 0, sb, st));
+    const int nseg = (n_iter + c - 1) / c;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int k0 = sg * c;
+        const int cnt = std::min(c, n_iter - k0);
+        CUBIC_CUDA(cudaMemcpyAsync(seg_u[0], ckpts + (size_t)sg * V, (size_t)V * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, st));
+        if ((s = enqueue_segment(p, image, eps, cnt, seg_u.data(), seg_b.data(), seg_r.data(), seg_q.data(), spec,
+                                 st)) != CUBIC_OK)
+            return s;
+        for (int j = cnt - 1; j >= 0; --j) {
+            // qbar = g u, ubar = g q
+            k_adj_q<<<gr, 256, 0, st>>>(g, seg_u[j], seg_q[j], tmp, ubar, V);
+            // Qbar, R -> G += conj(Qbar) R;  rbar = h * qbar
+            if ((s = enqueue_forward3(p, tmp, S1, 1.f, st)) != CUBIC_OK) return s;
+            if ((s = enqueue_forward3(p, seg_r[j], S2, 1.f, st)) != CUBIC_OK) return s;
+            k_spec_acc<<<gs, 256, 0, st>>>(G, S1, S2, rows, p->xh, p->xp, 0);
+            k_spec_mul<<<gs, 256, 0, st>>>(S1, p->H, rows, p->xh, p->xp, 0);
+            if ((s = enqueue_inverse3(p, S1, tmp, 1.f, st)) != CUBIC_OK) return s;
+            // dbar += rbar / c; bbar
+            k_adj_r<<<gr, 256, 0, st>>>(seg_b[j], image, tmp, dbar, eps, V);
+            // Bbar, U -> G += Bbar conj(U);  ubar += h (x) bbar
+            if ((s = enqueue_forward3(p, tmp, S1, 1.f, st)) != CUBIC_OK) return s;
+            if ((s = enqueue_forward3(p, seg_u[j], S2, 1.f, st)) != CUBIC_OK) return s;
+            k_spec_acc<<<gs, 256, 0, st>>>(G, S1, S2, rows, p->xh, p->xp, 1);
+            k_spec_mul<<<gs, 256, 0, st>>>(S1, p->H, rows, p->xh, p->xp, 1);
+            if ((s = enqueue_inverse3(p, S1, tmp, 1.f, st)) != CUBIC_OK) return s;
+            k_add<<<gr, 256, 0, st>>>(ubar, tmp, V);
+            std::swap(g, ubar);  // g = dL/du_k
+        }
+        CUBIC_CUDA(cudaGetLastError());
+    }
+    // the initial estimate u0 = max(mean(d), eps) depends on d
+    if (grad_image) {
+        k_sum_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(g, V, p->partial);
+        k_sum_final<<<1, kReduceThreads, 0, st>>>(p->partial, kReduceBlocks, p->partial + kReduceBlocks);
+        k_sum_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(image, V, red);
+        k_sum_final<<<1, kReduceThreads, 0, st>>>(red, kReduceBlocks, red + kReduceBlocks);
+        k_add_mean_grad<<<gr, 256, 0, st>>>(dbar, p->partial + kReduceBlocks, red + kReduceBlocks, V, eps);
+        CUBIC_CUDA(cudaMemcpyAsync(grad_image, dbar, (size_t)V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    if (grad_psf) {
+        if ((s = enqueue_inverse3(p, G, tmp, (float)(1.0 / (double)V), st)) != CUBIC_OK) return s;
+        k_origin_to_center<<<gr, 256, 0, st>>>(tmp, grad_psf, p->nz, p->ny, p->nx, accumulate_psf);
+    }
+    CUBIC_CUDA(cudaGetLastError());
+    return CUBIC_OK;
+}
+
+// ---- Gaussian PSF parameter gradient
+//
+// psf = A g / S, S = sum g, g = exp(-(dx^2+dy^2) a - dz^2 c), a = 1/(2 sxy^2), c = 1/(2 sz^2):
+//   dL/dA   = P / S,                          P = sum(pbar g)
+//   dL/dsxy = A/S (Pxy - P Sxy / S),          Pxy = sum(pbar g rxy/sxy^3), Sxy = sum(g rxy/sxy^3)
+//   dL/dsz  = A/S (Pz - P Sz / S)             (same with dz^2 / sz^3)
+// Six sums: S (the PSF's flux) in double; the five others in compensated float
+// (a Kahan running sum per thread, error-free TwoSum merges across threads).
+
+struct CFloat {
+    float s, c;  // value = s - c (c: Kahan compensation, the negated lost low part)
+};
+
+__device__ __forceinline__ CFloat cf_add(CFloat a, float x)
+{
+    const float y = x - a.c;
+    const float t = a.s + y;
+    a.c = (t - a.s) - y;
+    a.s = t;
+    return a;
+}
+
+__device__ __forceinline__ CFloat cf_merge(CFloat a, CFloat b)
+{
+    // TwoSum of the leading parts (s + err == a.s + b.s exactly), then the tails:
+    // value = s + err - a.c - b.c
+    const float s = a.s + b.s;
+    const float bb = s - a.s;
+    const float err = (a.s - (s - bb)) + (b.s - bb);
+    return CFloat{s, a.c + b.c - err};
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_psf_gauss_grad(const float *__restrict__ gp, int64_t nz,
+                                                                   int64_t ny, int64_t nx, float a_xy, float a_z,
+                                                                   float inv_sxy3, float inv_sz3,
+                                                                   double *__restrict__ part_S,
+                                                                   float *__restrict__ part5)
+{
+    __shared__ double shS[kReduceThreads];
+    __shared__ CFloat sh[5][kReduceThreads];
+    const int64_t V = nz * ny * nx;
+    double S = 0.0;
+    CFloat acc[5] = {};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        const float dx = (float)(i % nx - nx / 2);
+        const float dy = (float)((i / nx) % ny - ny / 2);
+        const float dz = (float)(i / (nx * ny) - nz / 2);
+        const float rxy = dx * dx + dy * dy, rz = dz * dz;
+        const float g = expf(-rxy * a_xy - rz * a_z);
+        const float gxy = g * rxy * inv_sxy3, gz = g * rz * inv_sz3;
+        const float pb = gp[i];
+        S += (double)g;
+        acc[0] = cf_add(acc[0], gxy);
+        acc[1] = cf_add(acc[1], gz);
+        acc[2] = cf_add(acc[2], pb * g);
+        acc[3] = cf_add(acc[3], pb * gxy);
+        acc[4] = cf_add(acc[4], pb * gz);
+    }
+    shS[threadIdx.x] = S;
+    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = kReduceThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            shS[threadIdx.x] += shS[threadIdx.x + w];
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = cf_merge(sh[k][threadIdx.x], sh[k][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part_S[blockIdx.x] = shS[0];
+        for (int k = 0; k < 5; ++k) {
+            part5[(blockIdx.x * 5 + k) * 2] = sh[k][0].s;
+            part5[(blockIdx.x * 5 + k) * 2 + 1] = sh[k][0].c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_psf_gauss_grad_final(const double *__restrict__ part_S,
+                                                                         const float *__restrict__ part5, int nblk,
+                                                                         float amp, float *__restrict__ out3)
+{
+    __shared__ double shS[kReduceThreads];
+    __shared__ CFloat sh[5][kReduceThreads];
+    double S = 0.0;
+    CFloat acc[5] = {};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        S += part_S[b];
+        for (int k = 0; k < 5; ++k)
+            acc[k] = cf_merge(acc[k], CFloat{part5[(b * 5 + k) * 2], part5[(b * 5 + k) * 2 + 1]});
+    }
+    shS[threadIdx.x] = S;
+    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = kReduceThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            shS[threadIdx.x] += shS[threadIdx.x + w];
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = cf_merge(sh[k][threadIdx.x], sh[k][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float Sf = (float)shS[0];
+        const float Sxy = sh[0][0].s - sh[0][0].c, Sz = sh[1][0].s - sh[1][0].c;
+        const float P = sh[2][0].s - sh[2][0].c, Pxy = sh[3][0].s - sh[3][0].c, Pz = sh[4][0].s - sh[4][0].c;
+        out3[0] = amp / Sf * (Pxy - P * Sxy / Sf);
+        out3[1] = amp / Sf * (Pz - P * Sz / Sf);
+        out3[2] = P / Sf;
+    }
+}
+
+extern "C" cubic_status_t cubic_psf_gaussian_backward(const int64_t dims[3], float sigma_xy, float sigma_z, float amp,
+                                                      const float *grad_psf, float *grad_params_dev, void *stream)
+{
+    if (!dims || !grad_psf || !grad_params_dev) return fail(CUBIC_ERR_INVALID_ARG, "null pointer");
+    for (int i = 0; i < 3; ++i)
+        if (dims[i] < 1) return fail(CUBIC_ERR_INVALID_ARG, "dims must be >= 1");
+    if (!(sigma_xy > 0.f) || !(sigma_z > 0.f) || !(sigma_xy < INFINITY) || !(sigma_z < INFINITY) ||
+        !(fabsf(amp) < INFINITY))
+        return fail(CUBIC_ERR_INVALID_ARG, "sigmas must be finite and > 0, amp finite");
+    if (!aligned16(grad_psf)) return fail(CUBIC_ERR_ALIGNMENT, "grad_psf must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *scratch = nullptr;
+    const size_t bytes = kReduceBlocks * sizeof(double) + kReduceBlocks * 10 * sizeof(float);
+    CUBIC_CUDA(cudaMallocAsync(&scratch, bytes, st));
+    double *part_S = (double *)scratch;
+    float *part5 = (float *)(part_S + kReduceBlocks);
+    const double sxy = sigma_xy, sz = sigma_z;
+    k_psf_gauss_grad<<<kReduceBlocks, kReduceThreads, 0, st>>>(grad_psf, dims[0], dims[1], dims[2],
+                                                               (float)(0.5 / (sxy * sxy)), (float)(0.5 / (sz * sz)),
+                                                               (float)(1.0 / (sxy * sxy * sxy)),
+                                                               (float)(1.0 / (sz * sz * sz)), part_S, part5);
+    k_psf_gauss_grad_final<<<1, kReduceThreads, 0, st>>>(part_S, part5, kReduceBlocks, amp, grad_params_dev);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return fail(CUBIC_ERR_CUDA, "psf gradient kernels: %s", cudaGetErrorString(e));
     return CUBIC_OK;
 }
 

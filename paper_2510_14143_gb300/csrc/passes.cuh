@@ -46,6 +46,11 @@ struct XArgs {
     int64_t xp;        // spectrum pitch (complex elements)
     float eps;
     unsigned *err;     // device error word (bounded waits)
+    // optional copies of intermediates (null: not stored), used by the gradient's
+    // recomputation: XM_RATIO stores b (keep_a) and r (keep_b); XM_UPDATE / XM_FINAL
+    // store q (keep_a)
+    float *keep_a;
+    float *keep_b;
 };
 
 struct YArgs {
@@ -199,6 +204,9 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             });
         } else if constexpr (MODE == XM_RATIO) {
             const float eps = a.eps;
+            float *kb0 = a.keep_a + r0 * N, *kb1 = a.keep_a + r1 * N;
+            float *kr0 = a.keep_b + r0 * N, *kr1 = a.keep_b + r1 * N;
+            const bool keep = a.keep_a != nullptr;
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
@@ -206,16 +214,27 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
                 // clamp keeps them >= eps)
                 const float x0 = ok0 ? __fdividef(p0[n], fmaxf(v[i].x, eps)) : 0.f;
                 const float x1 = ok1 ? __fdividef(p1[n], fmaxf(v[i].y, eps)) : 0.f;
+                if (keep) {
+                    if (ok0) { kb0[n] = v[i].x; kr0[n] = x0; }
+                    if (ok1) { kb1[n] = v[i].y; kr1[n] = x1; }
+                }
                 v[i] = make_float2(x0, x1);
             });
         } else if constexpr (MODE == XM_UPDATE || MODE == XM_FINAL) {
-            float *o0 = (MODE == XM_UPDATE ? a.u : a.dst) + r0 * N;
-            float *o1 = (MODE == XM_UPDATE ? a.u : a.dst) + r1 * N;
+            // the update writes to dst when given (out of place), else over u
+            float *ob = (MODE == XM_FINAL || a.dst) ? a.dst : a.u;
+            float *o0 = ob + r0 * N, *o1 = ob + r1 * N;
+            float *kq0 = a.keep_a + r0 * N, *kq1 = a.keep_a + r1 * N;
+            const bool keep = a.keep_a != nullptr;
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
                 const float x0 = ok0 ? p0[n] * v[i].x : 0.f;
                 const float x1 = ok1 ? p1[n] * v[i].y : 0.f;
+                if (keep) {
+                    if (ok0) kq0[n] = v[i].x;
+                    if (ok1) kq1[n] = v[i].y;
+                }
                 if (ok0) o0[n] = x0;
                 if (ok1) o1[n] = x1;
                 v[i] = make_float2(x0, x1);
