@@ -235,6 +235,8 @@ def run_ours(args, w: synth.Workload):
     }
     if not args.no_batched:
         result["batched"] = run_batched(cr, args)
+    if not args.no_grad:
+        result["fwd_bwd"] = run_fwd_bwd(cr, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, d_host, args.cpu_sample)
     if dist is not None:
@@ -283,6 +285,59 @@ def run_batched(cr, args):
             "voxels": vox, "value": round(vox * n_iter / (ms_b * 1e-3) / 1e9, 3), "unit": UNIT,
             "ms": round(ms_b, 3), "graph_kernel_nodes": nodes, "plain_calls_ms": round(ms_p, 3),
             "speedup_vs_plain_calls": round(ms_p / ms_b, 3)}
+
+
+def run_fwd_bwd(cr, args):
+    """16 volumes 128x128x64, 30 iterations, checkpoints every 6: forward + backward of an MSE loss
+    through the differentiable path, against 16 plain forwards."""
+    import torch
+    from paper_2510_14143_gb300.autograd import RLDeconvolve
+    vols = [synth.grad_volume(j) for j in range(synth.GRAD_COUNT)]
+    d = torch.from_numpy(np.stack([v[0] for v in vols])).cuda()
+    xt = torch.from_numpy(np.stack([v[1] for v in vols])).cuda()
+    sxy0, sz0, a0 = synth.GRAD_EVAL_PSF
+    n_iter, ckpt = synth.GRAD_ITERS, synth.GRAD_CKPT
+    shape = tuple(d.shape[1:])
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step():
+        dd = d.clone().requires_grad_(True)
+        p = [torch.tensor(v, device="cuda", requires_grad=True) for v in (sxy0, sz0, a0)]
+        u = RLDeconvolve.apply(dd, p[0], p[1], p[2], n_iter, 1e-6, ckpt)
+        loss = ((u - xt) ** 2).mean(dim=(1, 2, 3)).sum()
+        loss.backward()
+        return dd.grad, p
+
+    psf = torch.empty(shape, dtype=torch.float32, device="cuda")
+    cr.cubic_psf_gaussian(shape, sxy0, sz0, a0, psf)
+    plan = cr.cubic_rl_plan(shape, psf)
+    out = torch.empty_like(d)
+
+    def fwd_only():
+        for b in range(d.shape[0]):
+            cr.cubic_rl_deconvolve(plan, d[b], n_iter, 1e-6, out[b])
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(1, min(args.steps, 3))
+    ms_fb = timed(step, reps)
+    ms_f = timed(fwd_only, reps)
+    vox = int(d.numel())
+    return {"workload": f"{d.shape[0]} volumes 128x128x64, {n_iter} iterations, checkpoint every {ckpt}, "
+                        "MSE loss, grads wrt image and (sigma_xy, sigma_z, amp)",
+            "fwd_bwd_ms": round(ms_fb, 3), "fwd_plain_ms": round(ms_f, 3),
+            "fwd_bwd_over_fwd": round(ms_fb / ms_f, 3),
+            "value": round(vox * n_iter / (ms_fb * 1e-3) / 1e9, 3), "unit": "Gvoxel-iter/s (fwd+bwd)"}
 
 
 def load_traffic(kernel: str, w: synth.Workload):
@@ -398,6 +453,7 @@ def main():
     ap.add_argument("--cpu-sample", choices=("crop", "full"), default="full")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload leg")
+    ap.add_argument("--no-grad", action="store_true", help="skip the forward+backward leg")
     ap.add_argument("--ncu-target", metavar="VX,VY,VZ",
                     help="profiling target only: plan + --ncu-iters RL iterations with these launch shapes")
     ap.add_argument("--ncu-iters", type=int, default=1)
