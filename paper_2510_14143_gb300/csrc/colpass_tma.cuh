@@ -59,6 +59,11 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, int c0, int 
 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void bulk_wait_read()  // at most K store groups still reading shared memory
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(K) : "memory");
+}
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
@@ -86,35 +91,41 @@ constexpr size_t col_tile_bytes()
     return (size_t)N * B * sizeof(float2);
 }
 
-template <int N, int B, int KIND>
+template <int N, int P, int B, int KIND, int NS = 2>
 constexpr size_t col_smem_bytes()
 {
-    // 1 KB for the barriers (keeps the stages 1 KB aligned), two data stages,
-    // two H stages for the Z pass
-    return 1024 + 2 * col_stage_bytes<N, B>() * (KIND == COL_Z ? 2 : 1);
+    // 1 KB for the barriers (keeps the stages 1 KB aligned), NS data stages,
+    // NS H stages for the Z pass, then the stage twiddle table
+    return 1024 + NS * col_stage_bytes<N, B>() * (KIND == COL_Z ? 2 : 1) +
+           (size_t)tw_table_size(N, N / P) * sizeof(float2);
 }
 
-template <int N, int P, int B, int KIND>
+// NS shared-memory stages; tiles are prefetched D = max(1, NS - 2) ahead, so up to
+// NS - D - 1 tile stores may still be draining when a stage is refilled.
+template <int N, int P, int B, int KIND, int NS = 2>
 __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CUtensorMap tm_spec,
                                                       const __grid_constant__ CUtensorMap tm_h, ColArgs a)
 {
+    static_assert(NS >= 2 && NS <= 8, "stages");
+    constexpr int D = NS - 2 > 1 ? NS - 2 : 1;
+    constexpr int KW = NS - D - 1;  // store groups allowed in flight at a refill
     constexpr int E = N / P;
     constexpr int R = box_rows(N);
     constexpr int NB = N / R;  // boxes per tile
     constexpr size_t SB = col_stage_bytes<N, B>();
     extern __shared__ __align__(1024) unsigned char smem_col[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_col);  // full[0], full[1]
-    float2 *stage[2] = {reinterpret_cast<float2 *>(smem_col + 1024),
-                        reinterpret_cast<float2 *>(smem_col + 1024 + SB)};
-    float2 *hstage[2] = {reinterpret_cast<float2 *>(smem_col + 1024 + 2 * SB),
-                         reinterpret_cast<float2 *>(smem_col + 1024 + 3 * SB)};
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_col);  // full[0 .. NS)
+    auto stage = [&](int s) { return reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)s * SB); };
+    auto hstage = [&](int s) { return reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)(NS + s) * SB); };
     const bool needH = (KIND == COL_Z) && (a.mode == ZM_CONV || a.mode == ZM_CORR);
     const unsigned tile_bytes = (unsigned)(col_tile_bytes<N, B>() * (needH ? 2 : 1));
+    using FFT = LineFFT<N, P, true>;
+    float2 *stw = reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)NS * SB * (KIND == COL_Z ? 2 : 1));
 
     const int b = threadIdx.x % B;
     const int t = threadIdx.x / B;
     auto sync = [] { __syncthreads(); };
-    using FFT = LineFFT<N, P>;
+    FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * B);
 
     // tile -> tensor coordinates of its first box
     auto coords = [&](int64_t tile, int &cx, int &o) {
@@ -127,41 +138,45 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
         coords(tile, cx, o);
         mbar_arrive_expect_tx(&full[s], tile_bytes);
         for (int j = 0; j < NB; ++j) {
-            float2 *dst = stage[s] + (size_t)j * R * B;
+            float2 *dst = stage(s) + (size_t)j * R * B;
             if (KIND == COL_Y)
                 tma_load_3d(dst, &tm_spec, cx, j * R, o, &full[s]);
             else
                 tma_load_3d(dst, &tm_spec, cx, o, j * R, &full[s]);
-            if (needH) tma_load_3d(hstage[s] + (size_t)j * R * B, &tm_h, cx, o, j * R, &full[s]);
+            if (needH) tma_load_3d(hstage(s) + (size_t)j * R * B, &tm_h, cx, o, j * R, &full[s]);
         }
     };
 
     if (threadIdx.x == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+        for (int s = 0; s < NS; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    int64_t tile = blockIdx.x;
-    if (threadIdx.x == 0 && tile < a.ntiles) issue(tile, 0);
+    const int64_t first = blockIdx.x, step = gridDim.x;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < D; ++i)
+            if (first + i * step < a.ntiles) issue(first + i * step, i % NS);
 
-    for (int it = 0; tile < a.ntiles; tile += gridDim.x, ++it) {
-        const int s = it & 1;
-        const unsigned phase = (unsigned)((it >> 1) & 1);
-        const int64_t next = tile + gridDim.x;
-        if (threadIdx.x == 0 && next < a.ntiles) {
-            bulk_wait_read_all();  // the other stage's store has left shared memory
-            issue(next, s ^ 1);
+    int it = 0;
+    for (int64_t tile = first; tile < a.ntiles; tile += step, ++it) {
+        const int s = it % NS;
+        const unsigned phase = (unsigned)((it / NS) & 1);
+        const int64_t ahead = tile + (int64_t)D * step;
+        if (threadIdx.x == 0 && ahead < a.ntiles) {
+            bulk_wait_read<KW>();  // the stage being refilled has left shared memory
+            issue(ahead, (it + D) % NS);
         }
         const bool arrived = mbar_wait_bounded(&full[s], phase, a.err);
         if (!__syncthreads_and(arrived)) {
-            // give an already issued load of the next tile a bounded chance to land
-            if (threadIdx.x == 0 && next < a.ntiles)
-                mbar_wait_bounded(&full[s ^ 1], (unsigned)(((it + 1) >> 1) & 1), a.err);
+            // give already issued loads a bounded chance to land before leaving
+            if (threadIdx.x == 0)
+                for (int i = 1; i <= D; ++i)
+                    if (tile + (int64_t)i * step < a.ntiles)
+                        mbar_wait_bounded(&full[(it + i) % NS], (unsigned)(((it + i) / NS) & 1), a.err);
             break;
         }
 
-        float2 *buf = stage[s];
+        float2 *buf = stage(s);
         SmemStridedT<B> sm{buf + b};
         float2 v[E];
         const bool conj_in = (KIND == COL_Y) ? a.mode == 1 : a.mode == ZM_INV_SCALE;
@@ -171,16 +186,16 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
             v[i] = conj_in ? cconj(x) : x;
         });
         __syncthreads();  // every canonical read is done before the exchanges reuse the stage
-        FFT::forward(v, sm, a.tw, t, sync);
+        FFT::forward(v, sm, stw, t, sync);
         if (KIND == COL_Z && needH) {
-            const float2 *hb = hstage[s];
+            const float2 *hb = hstage(s);
             const bool corr = a.mode == ZM_CORR;
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const float2 h = hb[(t + P * i) * B + b];
                 v[i] = cconj(corr ? cmulconj(v[i], h) : cmul(v[i], h));
             });
-            FFT::forward(v, sm, a.tw, t, sync);
+            FFT::forward(v, sm, stw, t, sync);
             static_for<0, E>([&](auto i_) { v[CUBIC_CI(i_)] = cconj(v[CUBIC_CI(i_)]); });
         } else if (KIND == COL_Z) {
             const float sc = a.scale, sy = conj_in ? -a.scale : a.scale;

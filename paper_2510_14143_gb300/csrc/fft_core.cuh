@@ -132,6 +132,21 @@ constexpr int plan_span(int N, int E, int stage)
     return ns;
 }
 
+// Stage twiddle tables: for stage s >= 1 (radix R, span Ns) the table holds
+// W_{Ns R}^{k r} at [r][k] (r < R, k < Ns), so lanes with consecutive k read
+// consecutive words.  Tables of all stages are stored back to back.
+constexpr int tw_stage_offset(int N, int E, int stage)
+{
+    int off = 0;
+    for (int s = 1; s < stage; ++s) off += plan_radix(N, E, s) * plan_span(N, E, s);
+    return off;
+}
+
+constexpr int tw_table_size(int N, int E)
+{
+    return (N == 1) ? 0 : tw_stage_offset(N, E, plan_stages(N, E));
+}
+
 // Threads per line: fewest stages with at most Emax elements per thread,
 // ties broken towards E near 24.
 constexpr int choose_threads(int N, int Emax)
@@ -318,12 +333,33 @@ struct Dft {
 
 // ------------------------------------------------------------ line FFT
 
-template <int N, int P>
+// kSmemTw: `tw` is the stage table in shared memory (fill_twiddles); otherwise it
+// is the length-N table W_N^m in global memory.
+template <int N, int P, bool kSmemTw = false>
 struct LineFFT {
     static_assert(N % P == 0, "P must divide N");
     static constexpr int E = N / P;
     static constexpr int S = (N == 1) ? 0 : plan_stages(N, E);
     static_assert(S >= 0, "no radix plan for this (N, P)");
+    static constexpr int kTwSize = tw_table_size(N, E);
+
+    // Build the stage table in shared memory from the global W_N^m table
+    // (threads tid = 0 .. nthreads-1 cooperate; the caller synchronises after).
+    __device__ __forceinline__ static void fill_twiddles(float2 *smem_tw, const float2 *__restrict__ tw_global, int tid,
+                                                         int nthreads)
+    {
+        static_for<1, (S > 1 ? S : 1)>([&](auto s_) {
+            constexpr int s = CUBIC_CI(s_);
+            constexpr int R = plan_radix(N, E, s);
+            constexpr int Ns = plan_span(N, E, s);
+            constexpr int TS = N / (Ns * R);
+            float2 *dst = smem_tw + tw_stage_offset(N, E, s);
+            for (int i = tid; i < R * Ns; i += nthreads) {
+                const int r = i / Ns, k = i % Ns;
+                dst[i] = __ldg(tw_global + k * r * TS);
+            }
+        });
+    }
 
     // Forward transform of the canonical register set v of thread t.  `sm` maps
     // a line position to its shared-memory slot (sm.at(pos)); `sync`
@@ -349,10 +385,18 @@ struct LineFFT {
                 const int j = t + P * g;
                 const int k = j % Ns;
                 if constexpr (s > 0) {
-                    static_for<1, R>([&](auto r_) {
-                        constexpr int r = CUBIC_CI(r_);
-                        x[r] = cmul(x[r], __ldg(tw + k * r * TS));
-                    });
+                    if constexpr (kSmemTw) {
+                        const float2 *ts = tw + tw_stage_offset(N, E, s) + k;
+                        static_for<1, R>([&](auto r_) {
+                            constexpr int r = CUBIC_CI(r_);
+                            x[r] = cmul(x[r], ts[r * Ns]);
+                        });
+                    } else {
+                        static_for<1, R>([&](auto r_) {
+                            constexpr int r = CUBIC_CI(r_);
+                            x[r] = cmul(x[r], __ldg(tw + k * r * TS));
+                        });
+                    }
                 }
                 Dft<R>::run(x);
                 if constexpr (last) {

@@ -107,11 +107,12 @@ constexpr bool x_uses_tma()
     return (MODE == XM_RATIO || MODE == XM_UPDATE || MODE == XM_FINAL) && (N % 4 == 0);
 }
 
-template <int N, int L, int MODE>
+// shared memory: [mbarrier | operand rows (TMA modes) | stage twiddles | exchange lines]
+template <int N, int P, int L, int MODE>
 constexpr size_t x_smem_bytes()
 {
     return 16 + (x_uses_tma<N, MODE>() ? (size_t)L * 2 * N * sizeof(float) : 0) +
-           (size_t)L * x_smem_line<N>() * sizeof(float2);
+           (size_t)tw_table_size(N, N / P) * sizeof(float2) + (size_t)L * x_smem_line<N>() * sizeof(float2);
 }
 
 template <int N, int P, int L, int MODE>
@@ -120,9 +121,11 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     constexpr int E = N / P;
     constexpr bool kTma = x_uses_tma<N, MODE>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    using FFT = LineFFT<N, P, true>;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     float *oprows = reinterpret_cast<float *>(smem_raw + 16);
-    float2 *xch = reinterpret_cast<float2 *>(smem_raw + 16 + (kTma ? (size_t)L * 2 * N * sizeof(float) : 0));
+    float2 *stw = reinterpret_cast<float2 *>(smem_raw + 16 + (kTma ? (size_t)L * 2 * N * sizeof(float) : 0));
+    float2 *xch = stw + FFT::kTwSize;
 
     const int t = threadIdx.x % P;
     const int l = threadIdx.x / P;
@@ -131,14 +134,16 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     const bool ok0 = r0 < a.rows, ok1 = r1 < a.rows;
     SmemPadded sm{xch + l * x_smem_line<N>()};
     auto sync = [] { __syncthreads(); };
-    using FFT = LineFFT<N, P>;
 
+    FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * L);
     if constexpr (kTma) {
         if (threadIdx.x == 0) {
             mbar_init(bar, 1);
             mbar_fence_init();
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    if constexpr (kTma) {
         if (threadIdx.x == 0) {
             // this CTA's rows are contiguous: one copy
             const int64_t row0 = block * L * 2;
@@ -178,7 +183,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             }
             v[i] = make_float2(A.x - B.y, A.y + B.x);  // A + i B
         });
-        FFT::inverse(v, sm, a.tw, t, sync);
+        FFT::inverse(v, sm, stw, t, sync);
 
         // operand rows: shared memory (TMA) or global
         const float *p0, *p1;
@@ -243,7 +248,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     }
 
     if constexpr (MODE == XM_FWD || MODE == XM_RATIO || MODE == XM_UPDATE) {
-        FFT::forward(v, sm, a.tw, t, sync);
+        FFT::forward(v, sm, stw, t, sync);
         // split the packed spectrum into the two rows' half spectra
         static_for<0, E>([&](auto i_) {
             constexpr int i = CUBIC_CI(i_);
@@ -311,7 +316,9 @@ template <int N, int P, int B>
 __device__ __forceinline__ void y_body(const YArgs &a, const int64_t bx, const int64_t by)
 {
     constexpr int E = N / P;
+    using FFT = LineFFT<N, P, true>;
     extern __shared__ float2 smem_y[];
+    float2 *stw = smem_y + B * N;
     const int b = threadIdx.x % B;
     const int t = threadIdx.x / B;
     const int64_t col = a.col0 + bx * B + b;
@@ -319,6 +326,8 @@ __device__ __forceinline__ void y_body(const YArgs &a, const int64_t bx, const i
     float2 *base = a.spec + by * N * a.xp + col;
     SmemStrided sm{smem_y + b, B};
     auto sync = [] { __syncthreads(); };
+    FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * B);
+    __syncthreads();
     float2 v[E];
     const float sgn = a.inverse ? -1.f : 1.f;
     static_for<0, E>([&](auto i_) {
@@ -326,7 +335,7 @@ __device__ __forceinline__ void y_body(const YArgs &a, const int64_t bx, const i
         float2 x = ok ? base[(int64_t)(t + P * i) * a.xp] : make_float2(0.f, 0.f);
         v[i] = make_float2(x.x, sgn * x.y);
     });
-    LineFFT<N, P>::forward(v, sm, a.tw, t, sync);
+    FFT::forward(v, sm, stw, t, sync);
     if (ok) {
         static_for<0, E>([&](auto i_) {
             constexpr int i = CUBIC_CI(i_);
@@ -360,7 +369,9 @@ template <int N, int P, int B>
 __device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const int64_t by)
 {
     constexpr int E = N / P;
+    using FFT = LineFFT<N, P, true>;
     extern __shared__ float2 smem_z[];
+    float2 *stw = smem_z + B * N;
     const int b = threadIdx.x % B;
     const int t = threadIdx.x / B;
     const int64_t col = a.col0 + bx * B + b;
@@ -370,7 +381,8 @@ __device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const i
     float2 *base = a.spec + off;
     SmemStrided sm{smem_z + b, B};
     auto sync = [] { __syncthreads(); };
-    using FFT = LineFFT<N, P>;
+    FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * B);
+    __syncthreads();
     float2 v[E];
     const bool inv_only = a.mode == ZM_INV_SCALE;
     static_for<0, E>([&](auto i_) {
@@ -378,7 +390,7 @@ __device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const i
         const float2 x = ok ? base[(int64_t)(t + P * i) * zstride] : make_float2(0.f, 0.f);
         v[i] = inv_only ? cconj(x) : x;
     });
-    FFT::forward(v, sm, a.tw, t, sync);
+    FFT::forward(v, sm, stw, t, sync);
     if (a.mode == ZM_FWD_SCALE || inv_only) {
         const float s = a.scale, sy = inv_only ? -a.scale : a.scale;
         if (ok) {
@@ -399,7 +411,7 @@ __device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const i
         v[i] = cconj(p);
     });
     sync();  // the forward transform's last shared-memory reads are done
-    FFT::forward(v, sm, a.tw, t, sync);
+    FFT::forward(v, sm, stw, t, sync);
     if (ok) {
         static_for<0, E>([&](auto i_) {
             constexpr int i = CUBIC_CI(i_);

@@ -25,7 +25,7 @@ using XMultiLaunch = cudaError_t (*)(const MultiTable<XArgs> *, int64_t blocks, 
 using YMultiLaunch = cudaError_t (*)(const MultiTable<YArgs> *, int64_t blocks, int inverse, cudaStream_t);
 using ZMultiLaunch = cudaError_t (*)(const MultiTable<ZArgs> *, int64_t blocks, int mode, cudaStream_t);
 
-constexpr int kMaxVariants = 6;
+constexpr int kMaxVariants = 8;
 
 struct XVariant {
     int P = 0, L = 0;
@@ -68,7 +68,7 @@ cudaError_t launch_x(const XArgs &a, cudaStream_t st)
 {
     const int64_t pairs = (a.rows + 1) / 2;
     const int64_t grid = (pairs + L - 1) / L;
-    constexpr size_t smem = x_smem_bytes<N, L, MODE>();
+    constexpr size_t smem = x_smem_bytes<N, P, L, MODE>();
     auto fn = k_xpass<N, P, L, MODE>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
@@ -81,7 +81,7 @@ template <int N, int P, int B>
 cudaError_t launch_y(const YArgs &a, cudaStream_t st)
 {
     dim3 grid((unsigned)((a.col1 - a.col0 + B - 1) / B), (unsigned)a.nz);
-    constexpr size_t smem = sizeof(float2) * B * N;
+    constexpr size_t smem = sizeof(float2) * (B * N + tw_table_size(N, N / P));
     auto fn = k_ypass<N, P, B>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
@@ -94,7 +94,7 @@ template <int N, int P, int B>
 cudaError_t launch_z(const ZArgs &a, cudaStream_t st)
 {
     dim3 grid((unsigned)((a.col1 - a.col0 + B - 1) / B), (unsigned)a.ny);
-    constexpr size_t smem = sizeof(float2) * B * N;
+    constexpr size_t smem = sizeof(float2) * (B * N + tw_table_size(N, N / P));
     auto fn = k_zpass<N, P, B>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
@@ -102,6 +102,20 @@ cudaError_t launch_z(const ZArgs &a, cudaStream_t st)
     fn<<<grid, P * B, smem, st>>>(a, nullptr, a.mode);
     return cudaGetLastError();
 }
+
+// Default split: fewest radix stages with at most 32 (n >= 256) or 40 elements
+// per thread.  Alternative: at most 16 elements per thread (more threads, more
+// stages, fewer registers).
+template <int N>
+struct AxisShape {
+    static constexpr int P0 = (N == 1) ? 1 : choose_threads(N, N >= 256 ? 32 : 40);
+    static constexpr int P1 = (N == 1) ? 1 : choose_threads(N, 16);
+    static_assert(P0 > 0, "no thread split for this length");
+    static constexpr int lines(int P, int threads) { return P >= threads ? 1 : threads / P; }
+    // lengths that get tuned variants (the large, bandwidth-critical ones)
+    static constexpr bool kTuned = (N >= 64);
+    static constexpr bool kAlt = kTuned && P1 > 0 && P1 != P0 && P1 * 16 <= 1024;
+};
 
 // ------------------------------------------------------------------ TMA column passes
 
@@ -123,28 +137,28 @@ inline cudaError_t encode_spectrum_map(CUtensorMap *tm, const void *base, int64_
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int N, int P, int B, int KIND>
+template <int N, int P, int B, int KIND, int NS>
 int col_grid_cap()
 {
     static int cap = [] {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colpass_tma<N, P, B, KIND>, P * B,
-                                                      col_smem_bytes<N, B, KIND>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colpass_tma<N, P, B, KIND, NS>, P * B,
+                                                      col_smem_bytes<N, P, B, KIND, NS>());
         return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
     }();
     return cap;
 }
 
-template <int N, int P, int B, int KIND>
+template <int N, int P, int B, int KIND, int NS>
 cudaError_t launch_col(const float2 *spec, const float2 *H, int64_t nz, int64_t ny, int64_t xp, int64_t col0,
                        int64_t col1, int64_t outer, const float2 *tw, int mode, float scale, unsigned *err,
                        cudaStream_t st)
 {
     constexpr int R = box_rows(N);
-    constexpr size_t smem = col_smem_bytes<N, B, KIND>();
-    auto fn = k_colpass_tma<N, P, B, KIND>;
+    constexpr size_t smem = col_smem_bytes<N, P, B, KIND, NS>();
+    auto fn = k_colpass_tma<N, P, B, KIND, NS>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (col0 % B != 0) return cudaErrorInvalidValue;
@@ -167,29 +181,29 @@ cudaError_t launch_col(const float2 *spec, const float2 *H, int64_t nz, int64_t 
     c.scale = scale;
     c.err = err;
     if (c.ntiles == 0) return cudaSuccess;
-    const int64_t cap = col_grid_cap<N, P, B, KIND>();
+    const int64_t cap = col_grid_cap<N, P, B, KIND, NS>();
     const unsigned grid = (unsigned)(c.ntiles < cap ? c.ntiles : cap);
     fn<<<grid, P * B, smem, st>>>(tm_spec, tm_h, c);
     return cudaGetLastError();
 }
 
-template <int N, int P, int B>
+template <int N, int P, int B, int NS>
 cudaError_t launch_y_tma(const YArgs &a, cudaStream_t st)
 {
-    return launch_col<N, P, B, COL_Y>(a.spec, nullptr, a.nz, N, a.xp, a.col0, a.col1, a.nz, a.tw, a.inverse, 1.f,
+    return launch_col<N, P, B, COL_Y, NS>(a.spec, nullptr, a.nz, N, a.xp, a.col0, a.col1, a.nz, a.tw, a.inverse, 1.f,
                                       a.err, st);
 }
 
-template <int N, int P, int B>
+template <int N, int P, int B, int NS>
 cudaError_t launch_z_tma(const ZArgs &a, cudaStream_t st)
 {
     const bool needH = a.mode == ZM_CONV || a.mode == ZM_CORR;
-    return launch_col<N, P, B, COL_Z>(a.spec, needH ? a.H : nullptr, N, a.ny, a.xp, a.col0, a.col1, a.ny, a.tw,
+    return launch_col<N, P, B, COL_Z, NS>(a.spec, needH ? a.H : nullptr, N, a.ny, a.xp, a.col0, a.col1, a.ny, a.tw,
                                       a.mode, a.scale, a.err, st);
 }
 
-// Y and Z tile widths may differ: the Z pass also stages H.
-template <int N, int P, int BY, int BZ>
+// Y and Z tile widths and stage counts may differ: the Z pass also stages H.
+template <int N, int P, int BY, int NSY, int BZ, int NSZ>
 YZVariant make_yzvariant_tma()
 {
     YZVariant v;
@@ -197,27 +211,48 @@ YZVariant make_yzvariant_tma()
     v.B = BY;
     v.tma = true;
     if constexpr (BY > 0)
-        v.y = launch_y_tma<N, P, BY>;
+        v.y = launch_y_tma<N, P, BY, NSY>;
     else
         v.y = launch_y<N, P, 16>;
     if constexpr (BZ > 0)
-        v.z = launch_z_tma<N, P, BZ>;
+        v.z = launch_z_tma<N, P, BZ, NSZ>;
     else
         v.z = launch_z<N, P, 16>;
     return v;
 }
 
-// widest column tile (16 or 8) whose double-buffered stages fit in 200 KB
+constexpr size_t kTmaSmemBudget = 220 * 1024;
+
+// widest column tile (16 or 8) with at least two stages in the budget
 template <int N, int KIND>
 constexpr int tma_cols()
 {
-    return col_smem_bytes<N, 16, KIND>() <= 200 * 1024 ? 16 : col_smem_bytes<N, 8, KIND>() <= 200 * 1024 ? 8 : 0;
+    constexpr int P = AxisShape<N>::P0;
+    return col_smem_bytes<N, P, 16, KIND, 2>() <= kTmaSmemBudget ? 16
+           : col_smem_bytes<N, P, 8, KIND, 2>() <= kTmaSmemBudget ? 8
+                                                                   : 0;
+}
+
+// most stages (2..4) that fit the budget at that width, for thread split P.
+// CTAs of fewer than 256 threads keep two stages: they rely on several CTAs per
+// SM for issue slots, which deep stages would crowd out.
+template <int N, int P, int KIND>
+constexpr int tma_stages()
+{
+    constexpr int B = tma_cols<N, KIND>();
+    if constexpr (B == 0 || P * B < 256) {
+        return 2;
+    } else {
+        return col_smem_bytes<N, P, B, KIND, 4>() <= kTmaSmemBudget   ? 4
+               : col_smem_bytes<N, P, B, KIND, 3>() <= kTmaSmemBudget ? 3
+                                                                       : 2;
+    }
 }
 
 template <int N, int P, int L, int MODE>
 cudaError_t launch_x_multi(const MultiTable<XArgs> *tab, int64_t blocks, cudaStream_t st)
 {
-    constexpr size_t smem = x_smem_bytes<N, L, MODE>();
+    constexpr size_t smem = x_smem_bytes<N, P, L, MODE>();
     auto fn = k_xpass<N, P, L, MODE>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
@@ -229,7 +264,7 @@ cudaError_t launch_x_multi(const MultiTable<XArgs> *tab, int64_t blocks, cudaStr
 template <int N, int P, int B>
 cudaError_t launch_y_multi(const MultiTable<YArgs> *tab, int64_t blocks, int inverse, cudaStream_t st)
 {
-    constexpr size_t smem = sizeof(float2) * B * N;
+    constexpr size_t smem = sizeof(float2) * (B * N + tw_table_size(N, N / P));
     auto fn = k_ypass<N, P, B>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
@@ -241,7 +276,7 @@ cudaError_t launch_y_multi(const MultiTable<YArgs> *tab, int64_t blocks, int inv
 template <int N, int P, int B>
 cudaError_t launch_z_multi(const MultiTable<ZArgs> *tab, int64_t blocks, int mode, cudaStream_t st)
 {
-    constexpr size_t smem = sizeof(float2) * B * N;
+    constexpr size_t smem = sizeof(float2) * (B * N + tw_table_size(N, N / P));
     auto fn = k_zpass<N, P, B>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
@@ -277,20 +312,6 @@ YZVariant make_yzvariant()
 
 // ------------------------------------------------------------------ shapes
 
-// Default split: fewest radix stages with at most 32 (n >= 256) or 40 elements
-// per thread.  Alternative: at most 16 elements per thread (more threads, more
-// stages, fewer registers).
-template <int N>
-struct AxisShape {
-    static constexpr int P0 = (N == 1) ? 1 : choose_threads(N, N >= 256 ? 32 : 40);
-    static constexpr int P1 = (N == 1) ? 1 : choose_threads(N, 16);
-    static_assert(P0 > 0, "no thread split for this length");
-    static constexpr int lines(int P, int threads) { return P >= threads ? 1 : threads / P; }
-    // lengths that get tuned variants (the large, bandwidth-critical ones)
-    static constexpr bool kTuned = (N >= 64);
-    static constexpr bool kAlt = kTuned && P1 > 0 && P1 != P0 && P1 * 16 <= 1024;
-};
-
 template <int N>
 AxisKernels make_axis()
 {
@@ -314,9 +335,16 @@ AxisKernels make_axis()
     constexpr int BY = tma_cols<N, COL_Y>(), BZ = tma_cols<N, COL_Z>();
     if constexpr (S::kTuned && (BY > 0 || BZ > 0)) {
         // TMA-pipelined variants first: they are the defaults where they exist
-        k.yzv[k.nyz++] = make_yzvariant_tma<N, P0, BY, BZ>();
-        if constexpr (S::P1 > 0 && S::P1 != P0 && S::P1 * (BY > BZ ? BY : BZ) <= 1024 && S::P1 * 16 <= 1024)
-            k.yzv[k.nyz++] = make_yzvariant_tma<N, S::P1, BY, BZ>();
+        // deepest pipeline that fits, then two stages (more CTAs per SM)
+        constexpr int NY0 = tma_stages<N, P0, COL_Y>(), NZ0 = tma_stages<N, P0, COL_Z>();
+        k.yzv[k.nyz++] = make_yzvariant_tma<N, P0, BY, NY0, BZ, NZ0>();
+        if constexpr (NY0 > 2 || NZ0 > 2) k.yzv[k.nyz++] = make_yzvariant_tma<N, P0, BY, 2, BZ, 2>();
+        if constexpr (S::P1 > 0 && S::P1 != P0 && S::P1 * (BY > BZ ? BY : BZ) <= 1024 && S::P1 * 16 <= 1024) {
+            constexpr int P1 = S::P1;
+            constexpr int NY1 = tma_stages<N, P1, COL_Y>(), NZ1 = tma_stages<N, P1, COL_Z>();
+            k.yzv[k.nyz++] = make_yzvariant_tma<N, P1, BY, NY1, BZ, NZ1>();
+            if constexpr (NY1 > 2 || NZ1 > 2) k.yzv[k.nyz++] = make_yzvariant_tma<N, P1, BY, 2, BZ, 2>();
+        }
     }
     k.yzv[k.nyz++] = make_yzvariant<N, P0, 16>();
     if constexpr (S::kTuned) {
