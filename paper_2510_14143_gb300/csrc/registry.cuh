@@ -319,8 +319,16 @@ AxisKernels make_axis()
     AxisKernels k;
     k.n = N;
     constexpr int P0 = S::P0;
-    k.xv[0] = make_xvariant<N, P0, S::lines(P0, 128)>();
-    k.nx = 1;
+    // X default: for long lines the lighter split (<= 16 elements per thread, more
+    // CTAs per SM) measured faster; the other split stays available to the tuner
+    if constexpr (N >= 256 && S::kAlt) {
+        k.xv[0] = make_xvariant<N, S::P1, S::lines(S::P1, 128)>();
+        k.xv[1] = make_xvariant<N, P0, S::lines(P0, 128)>();
+        k.nx = 2;
+    } else {
+        k.xv[0] = make_xvariant<N, P0, S::lines(P0, 128)>();
+        k.nx = 1;
+    }
     constexpr int XL = S::lines(P0, 128);
     k.xm[XM_FWD] = launch_x_multi<N, P0, XL, XM_FWD>;
     k.xm[XM_INV] = launch_x_multi<N, P0, XL, XM_INV>;
@@ -351,7 +359,7 @@ AxisKernels make_axis()
         k.yzv[k.nyz++] = make_yzvariant<N, P0, 8>();
         if constexpr (S::kAlt) {
             constexpr int P1 = S::P1;
-            k.xv[k.nx++] = make_xvariant<N, P1, S::lines(P1, 128)>();
+            if constexpr (N < 256) k.xv[k.nx++] = make_xvariant<N, P1, S::lines(P1, 128)>();
             k.yzv[k.nyz++] = make_yzvariant<N, P1, 8>();
         }
     }

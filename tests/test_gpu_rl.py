@@ -258,3 +258,20 @@ def test_psf_gaussian_kernel_matches_oracle(cr):
         torch.cuda.synchronize()
         ref = oracle.psf_gaussian(shape, sxy, sz, amp)
         assert np.allclose(psf.cpu().numpy(), ref, rtol=2e-6, atol=1e-9 * amp)
+
+
+@pytest.mark.parametrize("shape", [(32, 64, 128), (12, 40, 1024), (9, 15, 64)])
+def test_every_x_variant_runs_rl(cr, shape):
+    # the pointwise Richardson-Lucy modes (ratio, update, final) of every X launch shape
+    d, _ = synth.make_volume(shape, 5, (1.5, 3.0), 10.0, 1.5, 2.5, 31 + sum(shape))
+    psf = oracle.psf_gaussian(shape, 1.5, 2.5).astype(np.float32)
+    ref = oracle.rl(d, psf, 4, 1e-6)
+    plan = cr.cubic_rl_plan(shape, dev(psf))
+    (nx, _, _), _ = cr.cubic_rl_plan_variants(plan)
+    dd = dev(d)
+    out = torch.empty_like(dd)
+    for vx in range(nx):
+        cr.cubic_rl_plan_set_variants(plan, vx, 0, 0)
+        cr.cubic_rl_deconvolve(plan, dd, 4, 1e-6, out)
+        torch.cuda.synchronize()
+        assert rel_l2(out.cpu().numpy(), ref) <= 2e-5, vx
