@@ -51,6 +51,56 @@ def dist_env():
     return rank, world, local
 
 
+class Ranks:
+    """The job's ranks (torchrun env): barrier and max-over-ranks of a scalar.
+
+    With WORLD_SIZE > 1 a process group is created (nccl for the GPU run, gloo
+    for host-only use); the only collectives are this barrier and this max.
+    """
+
+    def __init__(self, backend: str = "nccl"):
+        self.rank, self.world, self.local = dist_env()
+        self.backend = backend
+        self.dist = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            kw = {}
+            if backend == "nccl":
+                kw["device_id"] = torch.device("cuda", self.local)
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def _sync_device(self):
+        if self.backend == "nccl":
+            import torch
+            torch.cuda.synchronize()
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+        self._sync_device()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return float(x)
+        import torch
+        dev = torch.device("cuda", self.local) if self.backend == "nccl" else torch.device("cpu")
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput in G-units/s: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / (ms_max * 1e-3) / 1e9
+
+
 def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -130,22 +180,9 @@ def run_ours(args, w: synth.Workload):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks("nccl")
+    barrier = ranks.barrier
+    max_over_ranks = ranks.max
 
     shape, V, n_iter, eps = w.shape, w.voxels, w.n_iter, 1e-6
     d_host = make_inputs(w)
@@ -195,8 +232,8 @@ def run_ours(args, w: synth.Workload):
     ms_e2e = max_over_ranks(e0.elapsed_time(e1))
 
     units = V * n_iter * args.steps * world
-    value = units / (ms * 1e-3) / 1e9
-    e2e = units / (ms_e2e * 1e-3) / 1e9
+    value = job_rate(V * n_iter * args.steps, world, ms)
+    e2e = job_rate(V * n_iter * args.steps, world, ms_e2e)
 
     # roofline of the kernel with the largest share of device time
     kernels = {k: v for k, v in prof.items() if v["timed"] > 0}
@@ -239,8 +276,7 @@ def run_ours(args, w: synth.Workload):
         result["fwd_bwd"] = run_fwd_bwd(cr, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, d_host, args.cpu_sample)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return rank, result
 
 
