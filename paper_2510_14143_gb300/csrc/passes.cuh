@@ -84,9 +84,13 @@ struct ZArgs {
 
 // ------------------------------------------------------------------ X pass
 
-struct SmemPadded {  // element pos at base[pos + pos/32]
+// Element pos at base[pos + pos / R0] for an even first-stage radix R0 (its scattered
+// writes j*R0 + r then spread over all banks), at base[pos] for an odd one (j*R0 + r is
+// already conflict-free).
+template <int R0>
+struct SmemPadded {
     float2 *base;
-    __device__ __forceinline__ float2 &at(int pos) const { return base[pos + (pos >> 5)]; }
+    __device__ __forceinline__ float2 &at(int pos) const { return base[(R0 % 2 == 0) ? pos + pos / R0 : pos]; }
 };
 
 struct SmemStrided {  // element pos at base[pos * stride]
@@ -95,8 +99,23 @@ struct SmemStrided {  // element pos at base[pos * stride]
     __device__ __forceinline__ float2 &at(int pos) const { return base[pos * stride]; }
 };
 
+template <int N, int P>
+constexpr int x_first_radix() { return N == 1 ? 1 : plan_radix(N, N / P, 0); }
+
+// even number of complex elements >= nx/2+1: one spectrum row in a 16-byte multiple
 template <int N>
-constexpr int x_smem_line() { return N + (N >> 5) + 1; }
+constexpr int x_row_xb() { return ((N / 2 + 1) + 1) / 2 * 2; }
+
+// float2 slots per line pair: the padded exchange line, which also receives the
+// pair's two spectrum rows (2 * xb) at the start of the inverse passes
+template <int N, int P>
+constexpr int x_smem_line()
+{
+    constexpr int R0 = x_first_radix<N, P>();
+    constexpr int ex = N + ((R0 % 2 == 0) ? N / R0 : 0) + 1;
+    constexpr int sp = 2 * x_row_xb<N>();
+    return ((ex > sp ? ex : sp) + 1) / 2 * 2;
+}
 
 // The pointwise operand rows (d for the ratio, u for the update) are staged
 // into shared memory by one bulk TMA copy per CTA issued at kernel start, so
@@ -107,12 +126,13 @@ constexpr bool x_uses_tma()
     return (MODE == XM_RATIO || MODE == XM_UPDATE || MODE == XM_FINAL) && (N % 4 == 0);
 }
 
-// shared memory: [mbarrier | operand rows (TMA modes) | stage twiddles | exchange lines]
+// shared memory: [2 mbarriers | operand rows (TMA modes) | stage twiddles | line-pair regions]
 template <int N, int P, int L, int MODE>
 constexpr size_t x_smem_bytes()
 {
     return 16 + (x_uses_tma<N, MODE>() ? (size_t)L * 2 * N * sizeof(float) : 0) +
-           (size_t)tw_table_size(N, N / P) * sizeof(float2) + (size_t)L * x_smem_line<N>() * sizeof(float2);
+           (size_t)((tw_table_size(N, N / P) + 1) / 2 * 2) * sizeof(float2) +
+           (size_t)L * x_smem_line<N, P>() * sizeof(float2);
 }
 
 template <int N, int P, int L, int MODE>
@@ -122,27 +142,43 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     constexpr bool kTma = x_uses_tma<N, MODE>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using FFT = LineFFT<N, P, true>;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    constexpr int XB = x_row_xb<N>();
+    constexpr bool kSpecIn = MODE != XM_FWD;  // the pair's spectrum rows arrive by TMA
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);  // [0] operand rows, [1] spectrum rows
     float *oprows = reinterpret_cast<float *>(smem_raw + 16);
     float2 *stw = reinterpret_cast<float2 *>(smem_raw + 16 + (kTma ? (size_t)L * 2 * N * sizeof(float) : 0));
-    float2 *xch = stw + FFT::kTwSize;
+    float2 *xch = stw + (FFT::kTwSize + 1) / 2 * 2;  // 16-byte aligned: bulk-copy destination
 
     const int t = threadIdx.x % P;
     const int l = threadIdx.x / P;
     const int64_t m = block * L + l;
     const int64_t r0 = 2 * m, r1 = 2 * m + 1;
     const bool ok0 = r0 < a.rows, ok1 = r1 < a.rows;
-    SmemPadded sm{xch + l * x_smem_line<N>()};
+    float2 *lpair = xch + l * x_smem_line<N, P>();
+    SmemPadded<x_first_radix<N, P>()> sm{lpair};
     auto sync = [] { __syncthreads(); };
 
     FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * L);
-    if constexpr (kTma) {
+    if constexpr (kTma || kSpecIn) {
         if (threadIdx.x == 0) {
-            mbar_init(bar, 1);
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
             mbar_fence_init();
         }
     }
     __syncthreads();
+    if constexpr (kSpecIn) {
+        if (threadIdx.x == 0) {
+            // the CTA's spectrum rows, one bulk copy each, into the line-pair regions
+            const int64_t row0 = block * L * 2;
+            const int64_t left = a.rows - row0;
+            const int nr = (int)(left < 2 * L ? left : 2 * L);
+            mbar_arrive_expect_tx(&bar[1], (unsigned)(nr * XB * sizeof(float2)));
+            for (int r = 0; r < nr; ++r)
+                bulk_g2s(xch + (r >> 1) * x_smem_line<N, P>() + (r & 1) * XB, a.spec_in + (row0 + r) * a.xp,
+                         (unsigned)(XB * sizeof(float2)), &bar[1]);
+        }
+    }
     if constexpr (kTma) {
         if (threadIdx.x == 0) {
             // this CTA's rows are contiguous: one copy
@@ -151,8 +187,8 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             const int64_t nrows = left < 2 * L ? left : 2 * L;
             const float *src = (MODE == XM_RATIO ? a.d : a.u) + row0 * N;
             const unsigned bytes = (unsigned)(nrows * N * sizeof(float));
-            mbar_arrive_expect_tx(bar, bytes);
-            bulk_g2s(oprows, src, bytes, bar);
+            mbar_arrive_expect_tx(&bar[0], bytes);
+            bulk_g2s(oprows, src, bytes, &bar[0]);
         }
     }
 
@@ -165,7 +201,9 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             v[i] = make_float2(ok0 ? __ldg(s0 + n) : 0.f, ok1 ? __ldg(s1 + n) : 0.f);
         });
     } else {
-        const float2 *q0 = a.spec_in + r0 * a.xp, *q1 = a.spec_in + r1 * a.xp;
+        const bool landed = mbar_wait_bounded(&bar[1], 0, a.err);
+        if (!__syncthreads_and(landed)) return;
+        const float2 *q0 = lpair, *q1 = lpair + XB;
         static_for<0, E>([&](auto i_) {
             constexpr int i = CUBIC_CI(i_);
             const int k = t + P * i;
@@ -183,12 +221,13 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             }
             v[i] = make_float2(A.x - B.y, A.y + B.x);  // A + i B
         });
+        __syncthreads();  // the rows are read before the exchanges overwrite the region
         FFT::inverse(v, sm, stw, t, sync);
 
         // operand rows: shared memory (TMA) or global
         const float *p0, *p1;
         if constexpr (kTma) {
-            const bool arrived = mbar_wait_bounded(bar, 0, a.err);
+            const bool arrived = mbar_wait_bounded(&bar[0], 0, a.err);
             if (!__syncthreads_and(arrived)) return;
             p0 = oprows + (2 * l) * N;
             p1 = oprows + (2 * l + 1) * N;
