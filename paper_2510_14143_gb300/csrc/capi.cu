@@ -214,6 +214,10 @@ struct cubic_rl_plan_s {
     float *stage_in = nullptr, *stage_out = nullptr;  // device copies for host-buffer calls, owned
     unsigned char *bwd = nullptr;                      // gradient scratch, owned
     size_t bwd_bytes = 0;
+    // point-symmetric PSF: H is real and the Z passes read it as float (half the bytes)
+    bool allow_real_h = false;  // set by cubic_rl_plan (may allocate Hr)
+    bool use_real_h = false;
+    float *Hr = nullptr;        // [nz][ny][xp], owned
     // launch accounting and optional per-kernel CUDA-event timing
     int64_t launches[KK_COUNT] = {};
     double bytes[KK_COUNT] = {};
@@ -294,8 +298,8 @@ static cudaError_t run_y(cubic_rl_plan_s *p, const YArgs &a, cudaStream_t st)
 
 static cudaError_t run_z(cubic_rl_plan_s *p, const ZArgs &a, cudaStream_t st)
 {
-    static const int kind[4] = {KK_Z_FWD, KK_Z_CONV, KK_Z_CORR, KK_Z_INV};
-    const double arrays = (a.mode == ZM_CONV || a.mode == ZM_CORR) ? 3.0 : 2.0;
+    static const int kind[5] = {KK_Z_FWD, KK_Z_CONV, KK_Z_CORR, KK_Z_INV, KK_Z_CONV};
+    const double arrays = (a.mode == ZM_CONV || a.mode == ZM_CORR) ? 3.0 : a.mode == ZM_MUL_REAL ? 2.5 : 2.0;
     const double bytes = arrays * 8.0 * (double)p->rows * (double)(a.col1 - a.col0);
     return counted(p, kind[a.mode], st, [&] { return p->kz->yzv[p->vz].z(a, st); }, bytes);
 }
@@ -305,9 +309,17 @@ static YArgs y_args(const cubic_rl_plan_s *p, float2 *spec, int inverse, int64_t
     return YArgs{spec, p->tw_y, p->nz, p->xh, p->xp, inverse, c0, c1, p->err};
 }
 
+// the spectral product of a convolution (ZM_CONV) or correlation (ZM_CORR); with a real
+// H both are the same product
+static int conv_mode(const cubic_rl_plan_s *p, int zmode)
+{
+    return (p->use_real_h && (zmode == ZM_CONV || zmode == ZM_CORR)) ? (int)ZM_MUL_REAL : zmode;
+}
+
 static ZArgs z_args(const cubic_rl_plan_s *p, float2 *spec, int mode, float scale, int64_t c0, int64_t c1)
 {
-    return ZArgs{spec, p->H, p->tw_z, p->ny, p->xh, p->xp, mode, scale, c0, c1, p->err, p->nz};
+    return ZArgs{spec, p->H, p->tw_z, p->ny, p->xh, p->xp, conv_mode(p, mode), scale, c0, c1, p->err, p->nz,
+                 p->use_real_h ? p->Hr : nullptr};
 }
 
 static XArgs x_args(const cubic_rl_plan_s *p)
@@ -351,6 +363,31 @@ static cubic_status_t enqueue_yzy(cubic_rl_plan_s *p, float2 *spec, int zmode, c
     return CUBIC_OK;
 }
 
+// flag |= 1 unless h0(x) == h0(-x) for every x (bitwise): a point-symmetric PSF about
+// its centre, whose spectrum is real
+__global__ void k_check_even(const float *__restrict__ h0, int64_t nz, int64_t ny, int64_t nx, unsigned *flag)
+{
+    const int64_t V = nz * ny * nx;
+    bool odd = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+        const int64_t j = (((nz - z) % nz) * ny + (ny - y) % ny) * nx + (nx - x) % nx;
+        odd |= h0[i] != h0[j];
+    }
+    if (__syncthreads_or(odd) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
+// Hr = Re H and Im H = 0 (the spectrum of an even PSF, with the rounding noise of
+// the transform removed)
+__global__ void k_real_h(float2 *__restrict__ H, float *__restrict__ Hr, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 h = H[i];
+        Hr[i] = h.x;
+        H[i] = make_float2(h.x, 0.f);
+    }
+}
+
 static cubic_status_t load_psf(cubic_rl_plan_s *p, const float *psf, cudaStream_t st)
 {
     cubic_status_t s = ensure_workspace(p);
@@ -361,7 +398,29 @@ static cubic_status_t load_psf(cubic_rl_plan_s *p, const float *psf, cudaStream_
         k_center_to_origin<<<grid_for(p->V, 256), 256, 0, st>>>(psf, h0, p->nz, p->ny, p->nx);
         return cudaGetLastError();
     }));
-    return enqueue_forward3(p, h0, p->H, (float)(1.0 / (double)p->V), st);
+    bool even = false;
+    if (p->allow_real_h) {
+        // the reduction slot after the partial sums holds the flag for a moment
+        unsigned *flag = (unsigned *)(p->partial + kReduceBlocks);
+        CUBIC_CUDA(cudaMemsetAsync(flag, 0, sizeof(unsigned), st));
+        k_check_even<<<grid_for(p->V, 256), 256, 0, st>>>(h0, p->nz, p->ny, p->nx, flag);
+        unsigned host = 1;
+        CUBIC_CUDA(cudaMemcpyAsync(&host, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CUBIC_CUDA(cudaStreamSynchronize(st));
+        even = host == 0;
+    }
+    p->use_real_h = false;  // H itself is complex while it is computed
+    s = enqueue_forward3(p, h0, p->H, (float)(1.0 / (double)p->V), st);
+    if (s != CUBIC_OK || !even) return s;
+    if (!p->Hr) {
+        void *m = nullptr;
+        CUBIC_CUDA(cudaMalloc(&m, spec_elems(p) * sizeof(float)));
+        p->Hr = (float *)m;
+    }
+    k_real_h<<<grid_for((int64_t)spec_elems(p), 256), 256, 0, st>>>(p->H, p->Hr, (int64_t)spec_elems(p));
+    CUBIC_CUDA(cudaGetLastError());
+    p->use_real_h = true;
+    return CUBIC_OK;
 }
 
 // ------------------------------------------------------------------ tuning cache
@@ -448,6 +507,7 @@ extern "C" cubic_status_t cubic_rl_plan(cubic_rl_plan_t *plan, const int64_t dim
     p->kx = find_axis(p->nx);
     p->ky = find_axis(p->ny);
     p->kz = find_axis(p->nz);
+    p->allow_real_h = true;
 
     cubic_status_t s = CUBIC_OK;
     auto bail = [&](cubic_status_t st_) {
@@ -507,6 +567,7 @@ extern "C" cubic_status_t cubic_rl_plan_destroy(cubic_rl_plan_t plan)
     cudaFree(plan->stage_in);
     cudaFree(plan->stage_out);
     cudaFree(plan->bwd);
+    cudaFree(plan->Hr);
     for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
     delete plan;
     return CUBIC_OK;

@@ -117,8 +117,9 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_col);  // full[0 .. NS)
     auto stage = [&](int s) { return reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)s * SB); };
     auto hstage = [&](int s) { return reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)(NS + s) * SB); };
-    const bool needH = (KIND == COL_Z) && (a.mode == ZM_CONV || a.mode == ZM_CORR);
-    const unsigned tile_bytes = (unsigned)(col_tile_bytes<N, B>() * (needH ? 2 : 1));
+    const bool realH = (KIND == COL_Z) && a.mode == ZM_MUL_REAL;
+    const bool needH = (KIND == COL_Z) && (a.mode == ZM_CONV || a.mode == ZM_CORR || realH);
+    const unsigned tile_bytes = (unsigned)(col_tile_bytes<N, B>() * (needH ? (realH ? 3 : 4) : 2) / 2);
     using FFT = LineFFT<N, P, true>;
     float2 *stw = reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)NS * SB * (KIND == COL_Z ? 2 : 1));
 
@@ -143,7 +144,14 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
                 tma_load_3d(dst, &tm_spec, cx, j * R, o, &full[s]);
             else
                 tma_load_3d(dst, &tm_spec, cx, o, j * R, &full[s]);
-            if (needH) tma_load_3d(hstage(s) + (size_t)j * R * B, &tm_h, cx, o, j * R, &full[s]);
+            if (needH) {
+                // real H: float boxes of B columns (x in floats = cx / 2), packed half-size
+                if (realH)
+                    tma_load_3d(reinterpret_cast<float *>(hstage(s)) + (size_t)j * R * B, &tm_h, cx / 2, o, j * R,
+                                &full[s]);
+                else
+                    tma_load_3d(hstage(s) + (size_t)j * R * B, &tm_h, cx, o, j * R, &full[s]);
+            }
         }
     };
 
@@ -188,13 +196,22 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
         __syncthreads();  // every canonical read is done before the exchanges reuse the stage
         FFT::forward(v, sm, stw, t, sync);
         if (KIND == COL_Z && needH) {
-            const float2 *hb = hstage(s);
-            const bool corr = a.mode == ZM_CORR;
-            static_for<0, E>([&](auto i_) {
-                constexpr int i = CUBIC_CI(i_);
-                const float2 h = hb[(t + P * i) * B + b];
-                v[i] = cconj(corr ? cmulconj(v[i], h) : cmul(v[i], h));
-            });
+            if (realH) {
+                const float *hb = reinterpret_cast<const float *>(hstage(s));
+                static_for<0, E>([&](auto i_) {
+                    constexpr int i = CUBIC_CI(i_);
+                    const float h = hb[(t + P * i) * B + b];
+                    v[i] = make_float2(v[i].x * h, -v[i].y * h);
+                });
+            } else {
+                const float2 *hb = hstage(s);
+                const bool corr = a.mode == ZM_CORR;
+                static_for<0, E>([&](auto i_) {
+                    constexpr int i = CUBIC_CI(i_);
+                    const float2 h = hb[(t + P * i) * B + b];
+                    v[i] = cconj(corr ? cmulconj(v[i], h) : cmul(v[i], h));
+                });
+            }
             FFT::forward(v, sm, stw, t, sync);
             static_for<0, E>([&](auto i_) { v[CUBIC_CI(i_)] = cconj(v[CUBIC_CI(i_)]); });
         } else if (KIND == COL_Z) {

@@ -65,7 +65,9 @@ struct YArgs {
     unsigned *err;
 };
 
-enum ZMode : int { ZM_FWD_SCALE = 0, ZM_CONV = 1, ZM_CORR = 2, ZM_INV_SCALE = 3 };
+// ZM_MUL_REAL: product with a real H (point-symmetric PSF), where convolution and
+// correlation coincide
+enum ZMode : int { ZM_FWD_SCALE = 0, ZM_CONV = 1, ZM_CORR = 2, ZM_INV_SCALE = 3, ZM_MUL_REAL = 4 };
 
 struct ZArgs {
     float2 *spec;
@@ -80,6 +82,7 @@ struct ZArgs {
     int64_t col1;
     unsigned *err;
     int64_t nz;    // lines are this long (TMA path builds its tensor map from it)
+    const float *Hr;  // real H, float [nz][ny][xp] (ZM_MUL_REAL)
 };
 
 // ------------------------------------------------------------------ X pass
@@ -440,15 +443,24 @@ __device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const i
         }
         return;
     }
-    const float2 *hb = a.H + off;
     const bool corr = a.mode == ZM_CORR;
-    // product with H or conj(H), then conjugate for the inverse transform
-    static_for<0, E>([&](auto i_) {
-        constexpr int i = CUBIC_CI(i_);
-        const float2 h = ok ? __ldg(hb + (int64_t)(t + P * i) * zstride) : make_float2(0.f, 0.f);
-        const float2 p = corr ? cmulconj(v[i], h) : cmul(v[i], h);
-        v[i] = cconj(p);
-    });
+    if (a.mode == ZM_MUL_REAL) {
+        const float *hb = a.Hr + off;
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            const float h = ok ? __ldg(hb + (int64_t)(t + P * i) * zstride) : 0.f;
+            v[i] = make_float2(v[i].x * h, -v[i].y * h);
+        });
+    } else {
+        const float2 *hb = a.H + off;
+        // product with H or conj(H), then conjugate for the inverse transform
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            const float2 h = ok ? __ldg(hb + (int64_t)(t + P * i) * zstride) : make_float2(0.f, 0.f);
+            const float2 p = corr ? cmulconj(v[i], h) : cmul(v[i], h);
+            v[i] = cconj(p);
+        });
+    }
     sync();  // the forward transform's last shared-memory reads are done
     FFT::forward(v, sm, stw, t, sync);
     if (ok) {
@@ -468,7 +480,8 @@ __global__ void __launch_bounds__(P * B) k_zpass(ZArgs a, const MultiTable<ZArgs
     if (tab) {
         const int v = find_volume(tab->prefix, tab->nvol, blockIdx.x);
         a = tab->args[v];
-        a.mode = mode;
+        // a volume with a real H multiplies by it for both convolution and correlation
+        a.mode = (a.Hr && (mode == ZM_CONV || mode == ZM_CORR)) ? (int)ZM_MUL_REAL : mode;
         const int64_t local = (int64_t)blockIdx.x - tab->prefix[v];
         const int64_t nct = (a.col1 - a.col0 + B - 1) / B;
         bx = local % nct;

@@ -152,9 +152,9 @@ int col_grid_cap()
 }
 
 template <int N, int P, int B, int KIND, int NS>
-cudaError_t launch_col(const float2 *spec, const float2 *H, int64_t nz, int64_t ny, int64_t xp, int64_t col0,
-                       int64_t col1, int64_t outer, const float2 *tw, int mode, float scale, unsigned *err,
-                       cudaStream_t st)
+cudaError_t launch_col(const float2 *spec, const float2 *H, const float *Hr, int64_t nz, int64_t ny, int64_t xp,
+                       int64_t col0, int64_t col1, int64_t outer, const float2 *tw, int mode, float scale,
+                       unsigned *err, cudaStream_t st)
 {
     constexpr int R = box_rows(N);
     constexpr size_t smem = col_smem_bytes<N, P, B, KIND, NS>();
@@ -166,7 +166,19 @@ cudaError_t launch_col(const float2 *spec, const float2 *H, int64_t nz, int64_t 
     cudaError_t e = (KIND == COL_Y) ? encode_spectrum_map(&tm_spec, spec, nz, ny, xp, 2 * B, R, 1)
                                     : encode_spectrum_map(&tm_spec, spec, nz, ny, xp, 2 * B, 1, R);
     if (e != cudaSuccess) return e;
-    if (KIND == COL_Z && H) {
+    if (KIND == COL_Z && mode == ZM_MUL_REAL && Hr) {
+        // real H: float32 [nz][ny][xp], boxes of B floats
+        PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) return cudaErrorNotSupported;
+        const cuuint64_t dims[3] = {(cuuint64_t)xp, (cuuint64_t)ny, (cuuint64_t)nz};
+        const cuuint64_t strides[2] = {(cuuint64_t)(xp * sizeof(float)), (cuuint64_t)(xp * ny * sizeof(float))};
+        const cuuint32_t box[3] = {(cuuint32_t)B, 1, (cuuint32_t)R};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        if (enc(&tm_h, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(Hr), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    } else if (KIND == COL_Z && H) {
         e = encode_spectrum_map(&tm_h, H, nz, ny, xp, 2 * B, 1, R);
         if (e != cudaSuccess) return e;
     } else {
@@ -190,7 +202,7 @@ cudaError_t launch_col(const float2 *spec, const float2 *H, int64_t nz, int64_t 
 template <int N, int P, int B, int NS>
 cudaError_t launch_y_tma(const YArgs &a, cudaStream_t st)
 {
-    return launch_col<N, P, B, COL_Y, NS>(a.spec, nullptr, a.nz, N, a.xp, a.col0, a.col1, a.nz, a.tw, a.inverse, 1.f,
+    return launch_col<N, P, B, COL_Y, NS>(a.spec, nullptr, nullptr, a.nz, N, a.xp, a.col0, a.col1, a.nz, a.tw, a.inverse, 1.f,
                                       a.err, st);
 }
 
@@ -198,7 +210,7 @@ template <int N, int P, int B, int NS>
 cudaError_t launch_z_tma(const ZArgs &a, cudaStream_t st)
 {
     const bool needH = a.mode == ZM_CONV || a.mode == ZM_CORR;
-    return launch_col<N, P, B, COL_Z, NS>(a.spec, needH ? a.H : nullptr, N, a.ny, a.xp, a.col0, a.col1, a.ny, a.tw,
+    return launch_col<N, P, B, COL_Z, NS>(a.spec, needH ? a.H : nullptr, a.Hr, N, a.ny, a.xp, a.col0, a.col1, a.ny, a.tw,
                                       a.mode, a.scale, a.err, st);
 }
 
@@ -312,6 +324,16 @@ YZVariant make_yzvariant()
 
 // ------------------------------------------------------------------ shapes
 
+inline void push_yz(AxisKernels &k, const YZVariant &v)
+{
+    if (k.nyz < kMaxVariants) k.yzv[k.nyz++] = v;
+}
+
+inline void push_x(AxisKernels &k, const XVariant &v)
+{
+    if (k.nx < kMaxVariants) k.xv[k.nx++] = v;
+}
+
 template <int N>
 AxisKernels make_axis()
 {
@@ -345,22 +367,28 @@ AxisKernels make_axis()
         // TMA-pipelined variants first: they are the defaults where they exist
         // deepest pipeline that fits, then two stages (more CTAs per SM)
         constexpr int NY0 = tma_stages<N, P0, COL_Y>(), NZ0 = tma_stages<N, P0, COL_Z>();
-        k.yzv[k.nyz++] = make_yzvariant_tma<N, P0, BY, NY0, BZ, NZ0>();
-        if constexpr (NY0 > 2 || NZ0 > 2) k.yzv[k.nyz++] = make_yzvariant_tma<N, P0, BY, 2, BZ, 2>();
+        push_yz(k, make_yzvariant_tma<N, P0, BY, NY0, BZ, NZ0>());
+        if constexpr (NY0 > 2 || NZ0 > 2) push_yz(k, make_yzvariant_tma<N, P0, BY, 2, BZ, 2>());
         if constexpr (S::P1 > 0 && S::P1 != P0 && S::P1 * (BY > BZ ? BY : BZ) <= 1024 && S::P1 * 16 <= 1024) {
             constexpr int P1 = S::P1;
             constexpr int NY1 = tma_stages<N, P1, COL_Y>(), NZ1 = tma_stages<N, P1, COL_Z>();
-            k.yzv[k.nyz++] = make_yzvariant_tma<N, P1, BY, NY1, BZ, NZ1>();
-            if constexpr (NY1 > 2 || NZ1 > 2) k.yzv[k.nyz++] = make_yzvariant_tma<N, P1, BY, 2, BZ, 2>();
+            push_yz(k, make_yzvariant_tma<N, P1, BY, NY1, BZ, NZ1>());
+            if constexpr (NY1 > 2 || NZ1 > 2) push_yz(k, make_yzvariant_tma<N, P1, BY, 2, BZ, 2>());
+            // Z-oriented shapes (their Y kernel is the one above): three stages, or
+            // 32-column tiles
+            if constexpr (BZ == 16 && col_smem_bytes<N, P1, 16, COL_Z, 3>() <= kTmaSmemBudget)
+                push_yz(k, make_yzvariant_tma<N, P1, BY, NY1, 16, 3>());
+            if constexpr (BZ == 16 && P1 * 32 <= 1024 && col_smem_bytes<N, P1, 32, COL_Z, 2>() <= kTmaSmemBudget)
+                push_yz(k, make_yzvariant_tma<N, P1, BY, NY1, 32, 2>());
         }
     }
-    k.yzv[k.nyz++] = make_yzvariant<N, P0, 16>();
+    push_yz(k, make_yzvariant<N, P0, 16>());
     if constexpr (S::kTuned) {
-        k.yzv[k.nyz++] = make_yzvariant<N, P0, 8>();
+        push_yz(k, make_yzvariant<N, P0, 8>());
         if constexpr (S::kAlt) {
             constexpr int P1 = S::P1;
-            if constexpr (N < 256) k.xv[k.nx++] = make_xvariant<N, P1, S::lines(P1, 128)>();
-            k.yzv[k.nyz++] = make_yzvariant<N, P1, 8>();
+            if constexpr (N < 256) push_x(k, make_xvariant<N, P1, S::lines(P1, 128)>());
+            push_yz(k, make_yzvariant<N, P1, 8>());
         }
     }
     return k;

@@ -275,3 +275,28 @@ def test_every_x_variant_runs_rl(cr, shape):
         cr.cubic_rl_deconvolve(plan, dd, 4, 1e-6, out)
         torch.cuda.synchronize()
         assert rel_l2(out.cpu().numpy(), ref) <= 2e-5, vx
+
+
+def test_real_spectrum_used_for_symmetric_psf(cr):
+    # a point-symmetric PSF has a real spectrum: the Z passes then read H as float
+    # (2.5 instead of 3 spectrum-sized arrays per launch) and conv == corr
+    shape = (16, 32, 40)
+    d = synth.random_field(shape, 3, 1.0, 50.0)
+    sym = oracle.psf_gaussian(shape, 1.4, 2.2).astype(np.float32)
+    r = np.random.default_rng(5)
+    asym = (r.uniform(0.1, 1.0, shape) ** 3).astype(np.float32)
+    asym /= asym.sum()
+    rows, xh = shape[0] * shape[1], shape[2] // 2 + 1
+    for psf, real in ((sym, True), (asym, False)):
+        plan = cr.cubic_rl_plan(shape, dev(psf))
+        out = torch.empty(shape, dtype=torch.float32, device="cuda")
+        cr.cubic_rl_profile(plan, True)
+        cr.cubic_rl_deconvolve(plan, dev(d), 3, 1e-6, out)
+        prof = cr.cubic_rl_profile_read(plan)
+        torch.cuda.synchronize()
+        if real:
+            assert prof["z_corr"]["launches"] == 0 and prof["z_conv"]["launches"] == 6
+            assert prof["z_conv"]["bytes"] / 6 == pytest.approx(2.5 * 8 * rows * xh)
+        else:
+            assert prof["z_corr"]["launches"] == 3 and prof["z_conv"]["launches"] == 3
+        assert rel_l2(out.cpu().numpy(), oracle.rl(d, psf, 3, 1e-6)) <= 2e-5
