@@ -70,19 +70,31 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <int S>
-struct SmemStridedT {  // element pos at base[pos * S]
+// Exchange layout inside a stage: element pos of column b at base[(pos + pad(pos)) * S + b],
+// pad(pos) = pos / R0 for an even first-stage radix R0 (one spare row every R0 rows, so
+// the first stage's scattered writes j*R0 + r of the tile's different lines fall in
+// different banks), 0 for an odd one.  Tiles arrive and leave unpadded; the exchanges
+// only run after the tile's canonical reads and before its canonical writes.
+template <int S, int R0>
+struct SmemStridedT {
     float2 *base;
-    __device__ __forceinline__ float2 &at(int pos) const { return base[pos * S]; }
+    __device__ __forceinline__ float2 &at(int pos) const { return base[(pos + ((R0 % 2 == 0) ? pos / R0 : 0)) * S]; }
 };
 
-// one stage holds a tile; rounded up to 1 KB so that every stage (and every
-// box inside it, whose offsets are multiples of R*B*8 bytes) starts on the
-// alignment tensor copies need
-template <int N, int B>
+template <int N, int P>
+constexpr int col_pad_rows()
+{
+    constexpr int R0 = N == 1 ? 1 : plan_radix(N, N / P, 0);
+    return (R0 % 2 == 0) ? N / R0 : 0;
+}
+
+// one stage holds a tile plus the exchange padding; rounded up to 1 KB so that every
+// stage (and every box inside it, whose offsets are multiples of R*B*8 bytes) starts
+// on the alignment tensor copies need
+template <int N, int B, int P = N>
 constexpr size_t col_stage_bytes()
 {
-    return ((size_t)N * B * sizeof(float2) + 1023) / 1024 * 1024;
+    return ((size_t)(N + col_pad_rows<N, P>()) * B * sizeof(float2) + 1023) / 1024 * 1024;
 }
 
 template <int N, int B>
@@ -96,7 +108,7 @@ constexpr size_t col_smem_bytes()
 {
     // 1 KB for the barriers (keeps the stages 1 KB aligned), NS data stages,
     // NS H stages for the Z pass, then the stage twiddle table
-    return 1024 + NS * col_stage_bytes<N, B>() * (KIND == COL_Z ? 2 : 1) +
+    return 1024 + NS * col_stage_bytes<N, B, P>() * (KIND == COL_Z ? 2 : 1) +
            (size_t)tw_table_size(N, N / P) * sizeof(float2);
 }
 
@@ -112,7 +124,7 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
     constexpr int E = N / P;
     constexpr int R = box_rows(N);
     constexpr int NB = N / R;  // boxes per tile
-    constexpr size_t SB = col_stage_bytes<N, B>();
+    constexpr size_t SB = col_stage_bytes<N, B, P>();
     extern __shared__ __align__(1024) unsigned char smem_col[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_col);  // full[0 .. NS)
     auto stage = [&](int s) { return reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)s * SB); };
@@ -185,7 +197,7 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
         }
 
         float2 *buf = stage(s);
-        SmemStridedT<B> sm{buf + b};
+        SmemStridedT<B, (N == 1 ? 1 : plan_radix(N, N / P, 0))> sm{buf + b};
         float2 v[E];
         const bool conj_in = (KIND == COL_Y) ? a.mode == 1 : a.mode == ZM_INV_SCALE;
         static_for<0, E>([&](auto i_) {
