@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
     const int b = threadIdx.x % B;
     const int t = threadIdx.x / B;
     auto sync = [] { __syncthreads(); };
-    FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * B);
+    pdl_trigger();
+    FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * B);  // plan constant: before the wait
 
     // tile -> tensor coordinates of its first box
     auto coords = [&](int64_t tile, int &cx, int &o) {
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
         mbar_fence_init();
     }
     __syncthreads();
+    pdl_wait();  // the previous pass's output is complete from here on
     const int64_t first = blockIdx.x, step = gridDim.x;
     if (threadIdx.x == 0)
         for (int i = 0; i < D; ++i)

@@ -161,7 +161,8 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     SmemPadded<x_first_radix<N, P>()> sm{lpair};
     auto sync = [] { __syncthreads(); };
 
-    FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * L);
+    pdl_trigger();
+    FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * L);  // plan constant: before the wait
     if constexpr (kTma || kSpecIn) {
         if (threadIdx.x == 0) {
             mbar_init(&bar[0], 1);
@@ -170,6 +171,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
         }
     }
     __syncthreads();
+    pdl_wait();  // the previous pass's output is complete from here on
     if constexpr (kSpecIn) {
         if (threadIdx.x == 0) {
             // the CTA's spectrum rows, one bulk copy each, into the line-pair regions
@@ -368,8 +370,10 @@ __device__ __forceinline__ void y_body(const YArgs &a, const int64_t bx, const i
     float2 *base = a.spec + by * N * a.xp + col;
     SmemStrided sm{smem_y + b, B};
     auto sync = [] { __syncthreads(); };
+    pdl_trigger();
     FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * B);
     __syncthreads();
+    pdl_wait();
     float2 v[E];
     const float sgn = a.inverse ? -1.f : 1.f;
     static_for<0, E>([&](auto i_) {
@@ -423,8 +427,10 @@ __device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const i
     float2 *base = a.spec + off;
     SmemStrided sm{smem_z + b, B};
     auto sync = [] { __syncthreads(); };
+    pdl_trigger();
     FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * B);
     __syncthreads();
+    pdl_wait();
     float2 v[E];
     const bool inv_only = a.mode == ZM_INV_SCALE;
     static_for<0, E>([&](auto i_) {

@@ -12,6 +12,7 @@
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <utility>
 
 #include "colpass_tma.cuh"
 #include "passes.cuh"
@@ -57,6 +58,26 @@ const AxisKernels *find_axis(int64_t n);
 
 // ------------------------------------------------------------------ launchers
 
+// Launch with programmatic stream serialization: the kernel may start while its
+// predecessor in the stream is still running (its CTAs wait in pdl_wait before
+// touching the predecessor's output), which hides launch latency and prologues.
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
+}
+
 inline cudaError_t set_smem(const void *fn, size_t bytes)
 {
     if (bytes <= 48 * 1024) return cudaSuccess;
@@ -73,8 +94,7 @@ cudaError_t launch_x(const XArgs &a, cudaStream_t st)
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (grid == 0) return cudaSuccess;
-    fn<<<(unsigned)grid, P * L, smem, st>>>(a, nullptr);
-    return cudaGetLastError();
+    return launch_pdl(fn, dim3((unsigned)grid), dim3(P * L), smem, st, a, (const MultiTable<XArgs> *)nullptr);
 }
 
 template <int N, int P, int B>
@@ -86,8 +106,7 @@ cudaError_t launch_y(const YArgs &a, cudaStream_t st)
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    fn<<<grid, P * B, smem, st>>>(a, nullptr, a.inverse);
-    return cudaGetLastError();
+    return launch_pdl(fn, grid, dim3(P * B), smem, st, a, (const MultiTable<YArgs> *)nullptr, a.inverse);
 }
 
 template <int N, int P, int B>
@@ -99,8 +118,7 @@ cudaError_t launch_z(const ZArgs &a, cudaStream_t st)
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    fn<<<grid, P * B, smem, st>>>(a, nullptr, a.mode);
-    return cudaGetLastError();
+    return launch_pdl(fn, grid, dim3(P * B), smem, st, a, (const MultiTable<ZArgs> *)nullptr, a.mode);
 }
 
 // Default split: fewest radix stages with at most 32 (n >= 256) or 40 elements
@@ -195,8 +213,7 @@ cudaError_t launch_col(const float2 *spec, const float2 *H, const float *Hr, int
     if (c.ntiles == 0) return cudaSuccess;
     const int64_t cap = col_grid_cap<N, P, B, KIND, NS>();
     const unsigned grid = (unsigned)(c.ntiles < cap ? c.ntiles : cap);
-    fn<<<grid, P * B, smem, st>>>(tm_spec, tm_h, c);
-    return cudaGetLastError();
+    return launch_pdl(fn, dim3(grid), dim3(P * B), smem, st, tm_spec, tm_h, c);
 }
 
 template <int N, int P, int B, int NS>
@@ -269,8 +286,7 @@ cudaError_t launch_x_multi(const MultiTable<XArgs> *tab, int64_t blocks, cudaStr
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (blocks == 0) return cudaSuccess;
-    fn<<<(unsigned)blocks, P * L, smem, st>>>(XArgs{}, tab);
-    return cudaGetLastError();
+    return launch_pdl(fn, dim3((unsigned)blocks), dim3(P * L), smem, st, XArgs{}, tab);
 }
 
 template <int N, int P, int B>
@@ -281,8 +297,7 @@ cudaError_t launch_y_multi(const MultiTable<YArgs> *tab, int64_t blocks, int inv
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (blocks == 0) return cudaSuccess;
-    fn<<<(unsigned)blocks, P * B, smem, st>>>(YArgs{}, tab, inverse);
-    return cudaGetLastError();
+    return launch_pdl(fn, dim3((unsigned)blocks), dim3(P * B), smem, st, YArgs{}, tab, inverse);
 }
 
 template <int N, int P, int B>
@@ -293,8 +308,7 @@ cudaError_t launch_z_multi(const MultiTable<ZArgs> *tab, int64_t blocks, int mod
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (blocks == 0) return cudaSuccess;
-    fn<<<(unsigned)blocks, P * B, smem, st>>>(ZArgs{}, tab, mode);
-    return cudaGetLastError();
+    return launch_pdl(fn, dim3((unsigned)blocks), dim3(P * B), smem, st, ZArgs{}, tab, mode);
 }
 
 template <int N, int P, int L>

@@ -51,6 +51,13 @@ __device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gsrc, unsig
         : "memory");
 }
 
+// Programmatic dependent launch.  pdl_trigger: this CTA lets the next kernel in the
+// stream start launching (it runs only its constant prologue before pdl_wait).
+// pdl_wait: block until every grid this one depends on has completed and its memory
+// is visible.  Both are no-ops for a kernel launched without the PDL attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
 {
     unsigned done;
