@@ -69,6 +69,7 @@ def _load():
                 "orc_rl_iterate": ([P, P, P, cd, i64, i64, i64, P, P, P, P], ci),
                 "orc_rl": ([P, P, i64, i64, i64, ci, cd, P], ci),
                 "orc_rl_grad": ([P, P, i64, i64, i64, ci, cd, P, P, P], ci),
+                "orc_rl_auto": ([P, P, i64, i64, i64, ci, cd, cd, ci, P, ctypes.POINTER(ci), P], ci),
                 "orc_psf_gaussian": ([i64, i64, i64, cd, cd, cd, P], ci),
                 "orc_psf_gaussian_grad": ([i64, i64, i64, cd, cd, cd, P, P], ci),
             }
@@ -179,6 +180,17 @@ def rl(d, psf, n_iter: int, eps: float = 1e-6) -> np.ndarray:
     out = np.empty_like(dd)
     _check(_load().orc_rl(_p(dd), _p(p), *dd.shape, int(n_iter), float(eps), _p(out)), "rl")
     return out
+
+
+def rl_auto(d, psf, max_iter: int, eps: float, tol: float, check_every: int = 1):
+    """RL with automatic stopping; returns (estimate, iterations done, deltas)."""
+    dd, p = _f64(d), _f64(psf)
+    out = np.empty_like(dd)
+    hist = np.zeros(max(1, int(max_iter)), np.float64)
+    n = ctypes.c_int(0)
+    _check(_load().orc_rl_auto(_p(dd), _p(p), *dd.shape, int(max_iter), float(eps), float(tol), int(check_every),
+                               _p(out), ctypes.byref(n), _p(hist)), "rl_auto")
+    return out, int(n.value), hist[:n.value].copy()
 
 
 def rl_grad(d, psf, n_iter: int, eps: float, g_out):

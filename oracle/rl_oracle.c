@@ -370,6 +370,51 @@ int orc_rl(const double *d, const double *psf, int64_t nz, int64_t ny, int64_t n
     return rc;
 }
 
+/* RL with automatic stopping (the paper's Section 4, "automatic stopping criteria that
+ * monitor image quality improvement between consecutive iterations", with a threshold).
+ * Reading: the improvement of iteration k is the relative change of the estimate,
+ *   delta_k = ||u_{k+1} - u_k||_2 / ||u_k||_2,
+ * checked after every check_every-th iteration (and after the last one); the run stops
+ * at the first check with delta_k < tol.  Writes the estimate, the number of iterations
+ * done and delta_0 .. delta_{done-1} (history may be NULL). */
+int orc_rl_auto(const double *d, const double *psf, int64_t nz, int64_t ny, int64_t nx, int max_iter,
+                double eps, double tol, int check_every, double *out, int *n_done, double *history)
+{
+    if (!d || !psf || !out || !n_done || nz < 1 || ny < 1 || nx < 1 || max_iter < 1 || check_every < 1 ||
+        !(eps > 0))
+        return -1;
+    int64_t V = nz * ny * nx;
+    double *Hs = malloc(sizeof(double) * 2 * (size_t)V);
+    double *u = malloc(sizeof(double) * (size_t)V);
+    double *un = malloc(sizeof(double) * (size_t)V);
+    if (!Hs || !u || !un) { free(Hs); free(u); free(un); return -2; }
+    int rc = orc_psf_spectrum(psf, Hs, nz, ny, nx);
+    double u0 = orc_initial_value(d, V, eps);
+    for (int64_t i = 0; i < V; ++i) u[i] = u0;
+    int k = 0;
+    while (!rc && k < max_iter) {
+        rc = orc_rl_iterate(Hs, d, u, eps, nz, ny, nx, un, NULL, NULL, NULL);
+        if (rc) break;
+        double num = 0.0, den = 0.0;
+        for (int64_t i = 0; i < V; ++i) {
+            double e = un[i] - u[i];
+            num += e * e;
+            den += u[i] * u[i];
+        }
+        double delta = den > 0 ? sqrt(num / den) : 0.0;
+        if (history) history[k] = delta;
+        memcpy(u, un, sizeof(double) * (size_t)V);
+        ++k;
+        if ((k % check_every == 0 || k == max_iter) && delta < tol) break;
+    }
+    if (!rc) {
+        memcpy(out, u, sizeof(double) * (size_t)V);
+        *n_done = k;
+    }
+    free(Hs); free(u); free(un);
+    return rc;
+}
+
 /* Reverse mode through n_iter RL iterations.
  * g_out = dL/du_K.  Writes grad_d = dL/dd (through the ratio at every
  * iteration and through u0 = max(mean(d), eps)) and grad_psf = dL/dp for the

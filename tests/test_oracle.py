@@ -414,3 +414,46 @@ def test_rl_grad_zero_iterations():
     gd, gp = oracle.rl_grad(d, np.ones(shape) / 60, 0, 1e-6, g)
     assert np.allclose(gd, g.sum() / g.size)
     assert np.allclose(gp, 0.0)
+
+
+# ------------------------------------------------------- automatic stopping
+
+def test_rl_auto_delta_psf_stops_after_two():
+    # delta PSF: u1 = d, u2 = d, so delta_0 = ||d - u0|| / ||u0|| and delta_1 = 0
+    shape = (4, 6, 5)
+    d = np.random.default_rng(14).uniform(1, 100, shape)
+    psf = np.zeros(shape)
+    psf[tuple(n // 2 for n in shape)] = 1.0
+    out, n, hist = oracle.rl_auto(d, psf, 20, 1e-6, 1e-12, 1)
+    u0 = d.mean()
+    assert n == 2
+    assert np.isclose(hist[0], np.linalg.norm(d - u0) / (u0 * np.sqrt(d.size)), rtol=1e-12)
+    assert hist[1] < 1e-13               # zero up to the rounding of the FFT path
+    assert np.allclose(out, d, rtol=1e-12)
+
+
+def test_rl_auto_constant_image_stops_at_once():
+    shape = (4, 5, 6)
+    psf = np.random.default_rng(8).uniform(size=shape)
+    psf /= psf.sum()
+    out, n, hist = oracle.rl_auto(np.full(shape, 3.0), psf, 10, 1e-6, 1e-9, 1)
+    assert n == 1 and hist[0] < 1e-12 and np.allclose(out, 3.0)
+
+
+def test_rl_auto_history_and_check_cadence():
+    d, _ = synth.workload_volume(synth.SMALL)
+    psf = oracle.psf_gaussian(d.shape, 1.5, 3.0)
+    _, n_all, hist = oracle.rl_auto(d, psf, 12, 1e-6, 0.0, 1)       # tol 0: never stops early
+    assert n_all == 12
+    # delta_k from separately computed iterates (a second path through rl())
+    for k in (0, 3, 7):
+        uk = oracle.rl(d, psf, k, 1e-6)
+        uk1 = oracle.rl(d, psf, k + 1, 1e-6)
+        assert np.isclose(hist[k], np.linalg.norm(uk1 - uk) / np.linalg.norm(uk), rtol=1e-10)
+    # the first delta below a threshold is at index j; a check every 4 iterations stops at the
+    # first multiple of 4 whose own delta is below it
+    tol = 0.5 * (hist[5] + hist[6]) if hist[6] < hist[5] else hist[6] * 1.01
+    out, n, h = oracle.rl_auto(d, psf, 12, 1e-6, tol, 4)
+    checks = [k for k in range(4, 13, 4) if hist[k - 1] < tol]
+    assert n == (checks[0] if checks else 12)
+    assert np.allclose(out, oracle.rl(d, psf, n, 1e-6), rtol=1e-12)
