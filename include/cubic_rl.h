@@ -183,6 +183,19 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve_noalloc(const int64_t dims[3], cons
                                                      const float *image, int n_iter, float eps,
                                                      float *out, void *stream);
 
+/* Richardson-Lucy with automatic stopping.  The paper (Section 4) stops the iteration when
+ * the improvement between consecutive iterations falls under a threshold; it names neither
+ * the measure nor the threshold.  Reading taken here: the improvement of iteration k is the
+ * relative change of the estimate, delta_k = ||u_{k+1} - u_k||_2 / ||u_k||_2, accumulated
+ * inside the update pass.  After every check_every-th iteration (and after max_iter) the
+ * host reads delta_{k} (a stream synchronisation) and stops when delta_k < tol.
+ * out receives the last estimate, *n_done the number of iterations done, history (host,
+ * max_iter doubles, may be NULL) delta_0 .. delta_{n_done-1}.  Synchronous (returns after
+ * the last check).  Errors: INVALID_ARG, ALIGNMENT, OUT_OF_MEMORY, CUDA. */
+CUBIC_API cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const float *image, int max_iter,
+                                                  float eps, float tol, int check_every, float *out,
+                                                  int *n_done, double *history, void *stream);
+
 /* ---- differentiation (reverse mode through the iterations) ---- */
 
 /* cubic_rl_deconvolve that also stores the estimate u_k at every k = 0, ckpt_every,

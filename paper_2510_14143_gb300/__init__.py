@@ -62,6 +62,8 @@ _SIGS = {
     "cubic_rl_deconvolve_batched": ([ctypes.POINTER(_vp), _ci, ctypes.POINTER(_vp), _ci, _cf, ctypes.POINTER(_vp),
                                      _vp], _ci),
     "cubic_rl_batched_graph_nodes": ([], _i64),
+    "cubic_rl_deconvolve_auto": ([_vp, _vp, _ci, _cf, _cf, _ci, _vp, ctypes.POINTER(_ci),
+                                  ctypes.POINTER(ctypes.c_double), _vp], _ci),
     "cubic_rl_deconvolve_ckpt": ([_vp, _vp, _ci, _cf, _ci, _vp, _vp, _vp], _ci),
     "cubic_rl_backward_workspace_bytes": ([_vp, _ci, ctypes.POINTER(_sz)], _ci),
     "cubic_rl_backward": ([_vp, _vp, _ci, _cf, _ci, _vp, _vp, _vp, _vp, _ci, _vp], _ci),
@@ -288,6 +290,19 @@ def cubic_rl_deconvolve_batched(plans, images, n_iter: int, eps: float, outs, st
 
 def cubic_rl_batched_graph_nodes() -> int:
     return int(lib().cubic_rl_batched_graph_nodes())
+
+
+def cubic_rl_deconvolve_auto(plan: Plan, image, max_iter: int, eps: float, tol: float, check_every: int, out,
+                             stream=None):
+    """Automatic stopping; returns (iterations done, list of per-iteration relative changes)."""
+    import torch
+    n = _ci(0)
+    hist = (ctypes.c_double * max(1, int(max_iter)))()
+    _check(lib().cubic_rl_deconvolve_auto(plan.handle, _ptr(image, torch.float32, plan.voxels, "image"),
+                                          int(max_iter), float(eps), float(tol), int(check_every),
+                                          _ptr(out, torch.float32, plan.voxels, "out"), ctypes.byref(n), hist,
+                                          _stream(stream)), "cubic_rl_deconvolve_auto")
+    return int(n.value), list(hist[:n.value])
 
 
 def n_checkpoints(n_iter: int, ckpt_every: int) -> int:

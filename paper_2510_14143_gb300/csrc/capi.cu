@@ -215,6 +215,9 @@ struct cubic_rl_plan_s {
     unsigned char *bwd = nullptr;                      // gradient scratch, owned
     size_t bwd_bytes = 0;
     // point-symmetric PSF: H is real and the Z passes read it as float (half the bytes)
+    double *auto_stats = nullptr;  // automatic stopping: [iteration][64 slots][2], owned
+    double *auto_delta = nullptr;  // [iteration]
+    int auto_cap = 0;
     bool allow_real_h = false;  // set by cubic_rl_plan (may allocate Hr)
     bool use_real_h = false;
     float *Hr = nullptr;        // [nz][ny][xp], owned
@@ -568,6 +571,8 @@ extern "C" cubic_status_t cubic_rl_plan_destroy(cubic_rl_plan_t plan)
     cudaFree(plan->stage_out);
     cudaFree(plan->bwd);
     cudaFree(plan->Hr);
+    cudaFree(plan->auto_stats);
+    cudaFree(plan->auto_delta);
     for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
     delete plan;
     return CUBIC_OK;
@@ -1437,6 +1442,97 @@ extern "C" cubic_status_t cubic_psf_gaussian_backward(const int64_t dims[3], flo
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(scratch, st);
     if (e != cudaSuccess) return fail(CUBIC_ERR_CUDA, "psf gradient kernels: %s", cudaGetErrorString(e));
+    return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ automatic stopping
+//
+// The paper (Section 4) stops Richardson-Lucy automatically when the improvement
+// between consecutive iterations falls under a threshold.  Here the improvement of
+// iteration k is the relative change of the estimate,
+//   delta_k = ||u_{k+1} - u_k||_2 / ||u_k||_2,
+// whose two sums the update pass accumulates as it writes u_{k+1}.  Every check_every
+// iterations (and after the last) the host reads delta and stops below the threshold.
+
+__global__ void k_delta(const double *__restrict__ slots, double *__restrict__ delta)
+{
+    __shared__ double num[64], den[64];
+    const int i = threadIdx.x;
+    num[i] = slots[2 * i];
+    den[i] = slots[2 * i + 1];
+    __syncthreads();
+    for (int w = 32; w > 0; w >>= 1) {
+        if (i < w) {
+            num[i] += num[i + w];
+            den[i] += den[i + w];
+        }
+        __syncthreads();
+    }
+    if (i == 0) delta[0] = den[0] > 0.0 ? sqrt(num[0] / den[0]) : 0.0;
+}
+
+extern "C" cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const float *image, int max_iter, float eps,
+                                                   float tol, int check_every, float *out, int *n_done,
+                                                   double *history, void *stream)
+{
+    if (!plan || !image || !out || !n_done) return fail(CUBIC_ERR_INVALID_ARG, "plan, image, out, n_done must be non-null");
+    if (max_iter < 1 || check_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "max_iter and check_every must be >= 1");
+    if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
+    if (!(tol >= 0.f) || !(tol < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (!aligned16(image) || !aligned16(out)) return fail(CUBIC_ERR_ALIGNMENT, "image and out must be 16-byte aligned");
+    if (overlaps(image, out, (size_t)plan->V * sizeof(float))) return fail(CUBIC_ERR_INVALID_ARG, "out must not overlap image");
+    cubic_rl_plan_s *p = plan;
+    cubic_status_t s = ensure_workspace(p);
+    if (s != CUBIC_OK) return s;
+    if (p->auto_cap < max_iter) {
+        cudaDeviceSynchronize();
+        cudaFree(p->auto_stats);
+        cudaFree(p->auto_delta);
+        p->auto_stats = nullptr;
+        p->auto_delta = nullptr;
+        p->auto_cap = 0;
+        void *a = nullptr, *b = nullptr;
+        CUBIC_CUDA(cudaMalloc(&a, (size_t)max_iter * 128 * sizeof(double)));
+        p->auto_stats = (double *)a;
+        CUBIC_CUDA(cudaMalloc(&b, (size_t)max_iter * sizeof(double)));
+        p->auto_delta = (double *)b;
+        p->auto_cap = max_iter;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CUBIC_CUDA(cudaMemsetAsync(p->auto_stats, 0, (size_t)max_iter * 128 * sizeof(double), st));
+    if ((s = enqueue_init(p, image, eps, out, st)) != CUBIC_OK) return s;
+    XArgs xa = x_args(p);
+    xa.spec_in = p->ws;
+    xa.spec_out = p->ws;
+    xa.src = out;
+    xa.u = out;
+    xa.dst = out;
+    xa.d = image;
+    xa.eps = eps;
+    CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
+    int k = 0;
+    while (k < max_iter) {
+        if ((s = enqueue_yzy(p, p->ws, ZM_CONV, st)) != CUBIC_OK) return s;
+        CUBIC_CUDA(run_x(p, XM_RATIO, xa, st));
+        if ((s = enqueue_yzy(p, p->ws, ZM_CORR, st)) != CUBIC_OK) return s;
+        XArgs xs = xa;
+        xs.stats = p->auto_stats + (size_t)k * 128;
+        CUBIC_CUDA(run_x(p, k + 1 < max_iter ? XM_UPDATE : XM_FINAL, xs, st));
+        k_delta<<<1, 64, 0, st>>>(xs.stats, p->auto_delta + k);
+        CUBIC_CUDA(cudaGetLastError());
+        ++k;
+        if (k % check_every == 0 || k == max_iter) {
+            double delta = 0.0;
+            CUBIC_CUDA(cudaMemcpyAsync(&delta, p->auto_delta + k - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+            CUBIC_CUDA(cudaStreamSynchronize(st));
+            if (delta < (double)tol) break;  // out already holds u_k (the update wrote it)
+        }
+    }
+    *n_done = k;
+    if (history) {
+        CUBIC_CUDA(cudaMemcpyAsync(history, p->auto_delta, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUBIC_CUDA(cudaStreamSynchronize(st));
+    }
     return CUBIC_OK;
 }
 

@@ -51,6 +51,9 @@ struct XArgs {
     // store q (keep_a)
     float *keep_a;
     float *keep_b;
+    // optional (XM_UPDATE / XM_FINAL): adds sum((u_new - u)^2) and sum(u^2) into
+    // stats[2 s] and stats[2 s + 1], s = one of 64 slots (spread to avoid contention)
+    double *stats;
 };
 
 struct YArgs {
@@ -275,19 +278,44 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             float *o0 = ob + r0 * N, *o1 = ob + r1 * N;
             float *kq0 = a.keep_a + r0 * N, *kq1 = a.keep_a + r1 * N;
             const bool keep = a.keep_a != nullptr;
+            const bool stats = a.stats != nullptr;
+            float s_num = 0.f, s_den = 0.f;
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
-                const float x0 = ok0 ? p0[n] * v[i].x : 0.f;
-                const float x1 = ok1 ? p1[n] * v[i].y : 0.f;
+                const float u0v = ok0 ? p0[n] : 0.f, u1v = ok1 ? p1[n] : 0.f;
+                const float x0 = ok0 ? u0v * v[i].x : 0.f;
+                const float x1 = ok1 ? u1v * v[i].y : 0.f;
                 if (keep) {
                     if (ok0) kq0[n] = v[i].x;
                     if (ok1) kq1[n] = v[i].y;
+                }
+                if (stats) {
+                    s_num = fmaf(x0 - u0v, x0 - u0v, fmaf(x1 - u1v, x1 - u1v, s_num));
+                    s_den = fmaf(u0v, u0v, fmaf(u1v, u1v, s_den));
                 }
                 if (ok0) o0[n] = x0;
                 if (ok1) o1[n] = x1;
                 v[i] = make_float2(x0, x1);
             });
+            if (stats) {
+                // warp sums where the warp is full, else one add per thread
+                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                const int slot = (int)((block * ((P * L + 31) / 32) + warp) & 63);
+                if ((warp + 1) * 32 <= P * L) {
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s_num += __shfl_down_sync(0xffffffffu, s_num, o);
+                        s_den += __shfl_down_sync(0xffffffffu, s_den, o);
+                    }
+                    if (lane == 0) {
+                        atomicAdd(&a.stats[2 * slot], (double)s_num);
+                        atomicAdd(&a.stats[2 * slot + 1], (double)s_den);
+                    }
+                } else {
+                    atomicAdd(&a.stats[2 * slot], (double)s_num);
+                    atomicAdd(&a.stats[2 * slot + 1], (double)s_den);
+                }
+            }
         }
     }
 
