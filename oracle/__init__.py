@@ -69,6 +69,7 @@ def _load():
                 "orc_rl_iterate": ([P, P, P, cd, i64, i64, i64, P, P, P, P], ci),
                 "orc_rl": ([P, P, i64, i64, i64, ci, cd, P], ci),
                 "orc_rl_grad": ([P, P, i64, i64, i64, ci, cd, P, P, P], ci),
+                "orc_fsc": ([P, P, i64, i64, i64, ci, P, P, P, P], ci),
                 "orc_rl_auto": ([P, P, i64, i64, i64, ci, cd, cd, ci, P, ctypes.POINTER(ci), P], ci),
                 "orc_psf_gaussian": ([i64, i64, i64, cd, cd, cd, P], ci),
                 "orc_psf_gaussian_grad": ([i64, i64, i64, cd, cd, cd, P, P], ci),
@@ -191,6 +192,14 @@ def rl_auto(d, psf, max_iter: int, eps: float, tol: float, check_every: int = 1)
     _check(_load().orc_rl_auto(_p(dd), _p(p), *dd.shape, int(max_iter), float(eps), float(tol), int(check_every),
                                _p(out), ctypes.byref(n), _p(hist)), "rl_auto")
     return out, int(n.value), hist[:n.value].copy()
+
+
+def fsc(a, b, n_shells: int):
+    """Fourier Shell Correlation per shell; returns (fsc, num, |A|^2 sums, |B|^2 sums)."""
+    aa, bb = _f64(a), _f64(b)
+    outs = [np.zeros(int(n_shells), np.float64) for _ in range(4)]
+    _check(_load().orc_fsc(_p(aa), _p(bb), *aa.shape, int(n_shells), *[_p(o) for o in outs]), "fsc")
+    return tuple(outs)
 
 
 def rl_grad(d, psf, n_iter: int, eps: float, g_out):

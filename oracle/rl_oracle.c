@@ -415,6 +415,60 @@ int orc_rl_auto(const double *d, const double *psf, int64_t nz, int64_t ny, int6
     return rc;
 }
 
+/* Fourier Shell Correlation of two volumes (the paper's FRC/FSC resolution metric,
+ * Section 3 "custom algorithms" and Section 4 "Evaluation metrics"):
+ *   FSC(s) = Re sum_{k in s} A(k) conj B(k) / sqrt(sum_{k in s} |A(k)|^2 sum_{k in s} |B(k)|^2),
+ * A, B the full 3D DFTs.  Shell s = floor(2 * n_shells * rho) for the normalised radius
+ * rho = |(fz, fy, fx)|, f = signed frequency / n (cycles per voxel), evaluated exactly in
+ * integers (rho^2 is rational); rho >= 1/2 (beyond Nyquist) is left out.  num, da, db: the three sums per shell (may be NULL); fsc: the
+ * ratio (0 for an empty shell). */
+int orc_fsc(const double *a, const double *b, int64_t nz, int64_t ny, int64_t nx, int n_shells, double *fsc,
+            double *num, double *da, double *db)
+{
+    if (!a || !b || !fsc || nz < 1 || ny < 1 || nx < 1 || n_shells < 1) return -1;
+    int64_t V = nz * ny * nx;
+    cplx *A = malloc(sizeof(cplx) * (size_t)V), *B = malloc(sizeof(cplx) * (size_t)V);
+    double *sn = calloc((size_t)n_shells, sizeof(double)), *sa = calloc((size_t)n_shells, sizeof(double));
+    double *sb = calloc((size_t)n_shells, sizeof(double));
+    int rc = -2;
+    if (A && B && sn && sa && sb) {
+        for (int64_t i = 0; i < V; ++i) { A[i] = a[i]; B[i] = b[i]; }
+        rc = fft3(A, nz, ny, nx, 0);
+        if (!rc) rc = fft3(B, nz, ny, nx, 0);
+        if (!rc) {
+            for (int64_t z = 0; z < nz; ++z)
+                for (int64_t y = 0; y < ny; ++y)
+                    for (int64_t x = 0; x < nx; ++x) {
+                        /* signed frequency index in (-n/2, n/2]; rho^2 = num / den exactly */
+                        __int128 kz = 2 * z > nz ? z - nz : z, ky = 2 * y > ny ? y - ny : y;
+                        __int128 kx = 2 * x > nx ? x - nx : x;
+                        __int128 den = (__int128)nz * nz * ny * ny * nx * nx;
+                        __int128 rn = kz * kz * ny * ny * nx * nx + ky * ky * nz * nz * nx * nx +
+                                      kx * kx * nz * nz * ny * ny;
+                        /* s = floor(2 S rho) = isqrt(floor(4 S^2 num / den)) */
+                        __int128 q = (__int128)4 * n_shells * n_shells * rn / den;
+                        int64_t s = (int64_t)floor(sqrt((double)q));
+                        while ((__int128)s * s > q) --s;
+                        while ((__int128)(s + 1) * (s + 1) <= q) ++s;
+                        if (s >= n_shells) continue; /* rho >= 1/2 */
+                        int64_t i = (z * ny + y) * nx + x;
+                        sn[s] += creal(A[i] * conj(B[i]));
+                        sa[s] += creal(A[i] * conj(A[i]));
+                        sb[s] += creal(B[i] * conj(B[i]));
+                    }
+            for (int s = 0; s < n_shells; ++s) {
+                double den = sqrt(sa[s] * sb[s]);
+                fsc[s] = den > 0 ? sn[s] / den : 0.0;
+                if (num) num[s] = sn[s];
+                if (da) da[s] = sa[s];
+                if (db) db[s] = sb[s];
+            }
+        }
+    }
+    free(A); free(B); free(sn); free(sa); free(sb);
+    return rc;
+}
+
 /* Reverse mode through n_iter RL iterations.
  * g_out = dL/du_K.  Writes grad_d = dL/dd (through the ratio at every
  * iteration and through u0 = max(mean(d), eps)) and grad_psf = dL/dp for the

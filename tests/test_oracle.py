@@ -457,3 +457,59 @@ def test_rl_auto_history_and_check_cadence():
     checks = [k for k in range(4, 13, 4) if hist[k - 1] < tol]
     assert n == (checks[0] if checks else 12)
     assert np.allclose(out, oracle.rl(d, psf, n, 1e-6), rtol=1e-12)
+
+
+# ------------------------------------------------------- Fourier Shell Correlation
+
+def _tone(shape, k):
+    idx = np.indices(shape).astype(float)
+    return np.cos(2 * np.pi * sum(k[i] * idx[i] / shape[i] for i in range(3)))
+
+
+def test_fsc_identity_sign_and_scale():
+    shape = (8, 12, 10)
+    a = np.random.default_rng(1).standard_normal(shape)
+    f, num, da, db = oracle.fsc(a, a, 6)
+    nonempty = da > 0
+    assert np.allclose(f[nonempty], 1.0, atol=1e-12)
+    assert np.allclose(oracle.fsc(a, -2.5 * a, 6)[0][nonempty], -1.0, atol=1e-12)
+    assert np.allclose(oracle.fsc(a, 3.0 * a, 6)[0][nonempty], 1.0, atol=1e-12)
+
+
+def test_fsc_single_tone_closed_forms():
+    shape = (8, 16, 12)
+    k0 = (1, 3, 2)
+    a = _tone(shape, k0)
+    V = a.size
+    rho = np.sqrt(sum((k0[i] / shape[i]) ** 2 for i in range(3)))
+    n_sh = 10
+    s0 = int(np.floor(2 * n_sh * rho))
+    f, num, da, db = oracle.fsc(a, a, n_sh)
+    # all energy in one shell: |A(+-k0)| = V/2, so sum |A|^2 = V^2 / 2
+    assert np.isclose(da[s0], V * V / 2, rtol=1e-12)
+    assert np.allclose(np.delete(da, s0), 0.0, atol=1e-9 * V * V)
+    # a circular shift by s multiplies A by exp(-2 pi i k.s / n): FSC = cos(2 pi k0.s / n)
+    s = (2, 5, 1)
+    b = np.roll(a, s, axis=(0, 1, 2))
+    phase = 2 * np.pi * sum(k0[i] * s[i] / shape[i] for i in range(3))
+    assert np.isclose(oracle.fsc(a, b, n_sh)[0][s0], np.cos(phase), atol=1e-12)
+
+
+def test_fsc_excludes_beyond_nyquist_and_counts_both_halves():
+    # a tone at the corner (rho > 1/2) contributes nothing; Parseval over shells for a
+    # field with no energy beyond Nyquist
+    shape = (8, 8, 8)
+    corner = _tone(shape, (4, 4, 4))
+    assert np.allclose(oracle.fsc(corner, corner, 4)[2], 0.0, atol=1e-9)
+    lowpass = _tone(shape, (1, 0, 0)) + 0.5 * _tone(shape, (0, 2, 1)) + 0.25
+    _, _, da, _ = oracle.fsc(lowpass, lowpass, 8)
+    assert np.isclose(da.sum(), lowpass.size * (lowpass ** 2).sum(), rtol=1e-12)
+
+
+def test_fsc_shell_edges_exact():
+    # tones sitting exactly on shell edges: rho = 1/4 with 4 shells -> shell 2, rho = 1/8 -> shell 1
+    shape = (8, 8, 8)
+    for k0, shell in (((0, 2, 0), 2), ((0, 0, 1), 1), ((2, 0, 0), 2)):
+        a = _tone(shape, k0)
+        _, _, da, _ = oracle.fsc(a, a, 4)
+        assert da[shell] > 0 and np.count_nonzero(da > 1e-9) == 1, (k0, da)
