@@ -196,6 +196,17 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const fl
                                                   float eps, float tol, int check_every, float *out,
                                                   int *n_done, double *history, void *stream);
 
+/* Fourier Shell Correlation of two volumes of the plan's dims, the resolution metric the
+ * paper evaluates deconvolution with (FRC/FSC, Sections 3 and 4):
+ *   fsc[s] = Re sum_{k in s} A(k) conj B(k) / sqrt(sum |A|^2 sum |B|^2),
+ * A, B the 3D DFTs of a and b (device float32 volumes).  Shell s = floor(2 n_shells rho)
+ * for the normalised frequency radius rho = |(kz/nz, ky/ny, kx/nx)| (cycles per voxel,
+ * decided exactly in integer arithmetic); frequencies beyond Nyquist (rho >= 1/2) are left
+ * out; an empty shell gives 0.  fsc: device float32[n_shells].  1 <= n_shells <= 1024.
+ * Uses the plan's workspace and a second spectrum it allocates on first use. */
+CUBIC_API cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const float *b, int n_shells,
+                                   float *fsc, void *stream);
+
 /* ---- differentiation (reverse mode through the iterations) ---- */
 
 /* cubic_rl_deconvolve that also stores the estimate u_k at every k = 0, ckpt_every,

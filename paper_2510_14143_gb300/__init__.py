@@ -62,6 +62,7 @@ _SIGS = {
     "cubic_rl_deconvolve_batched": ([ctypes.POINTER(_vp), _ci, ctypes.POINTER(_vp), _ci, _cf, ctypes.POINTER(_vp),
                                      _vp], _ci),
     "cubic_rl_batched_graph_nodes": ([], _i64),
+    "cubic_fsc": ([_vp, _vp, _vp, _ci, _vp, _vp], _ci),
     "cubic_rl_deconvolve_auto": ([_vp, _vp, _ci, _cf, _cf, _ci, _vp, ctypes.POINTER(_ci),
                                   ctypes.POINTER(ctypes.c_double), _vp], _ci),
     "cubic_rl_deconvolve_ckpt": ([_vp, _vp, _ci, _cf, _ci, _vp, _vp, _vp], _ci),
@@ -303,6 +304,17 @@ def cubic_rl_deconvolve_auto(plan: Plan, image, max_iter: int, eps: float, tol: 
                                           _ptr(out, torch.float32, plan.voxels, "out"), ctypes.byref(n), hist,
                                           _stream(stream)), "cubic_rl_deconvolve_auto")
     return int(n.value), list(hist[:n.value])
+
+
+def cubic_fsc(plan: Plan, a, b, n_shells: int, fsc=None, stream=None):
+    """Fourier Shell Correlation of two volumes; returns the float32 CUDA tensor of n_shells values."""
+    import torch
+    if fsc is None:
+        fsc = torch.empty(int(n_shells), dtype=torch.float32, device="cuda")
+    _check(lib().cubic_fsc(plan.handle, _ptr(a, torch.float32, plan.voxels, "a"),
+                           _ptr(b, torch.float32, plan.voxels, "b"), int(n_shells),
+                           _ptr(fsc, torch.float32, int(n_shells), "fsc"), _stream(stream)), "cubic_fsc")
+    return fsc
 
 
 def n_checkpoints(n_iter: int, ckpt_every: int) -> int:

@@ -215,6 +215,9 @@ struct cubic_rl_plan_s {
     unsigned char *bwd = nullptr;                      // gradient scratch, owned
     size_t bwd_bytes = 0;
     // point-symmetric PSF: H is real and the Z passes read it as float (half the bytes)
+    float2 *ws2 = nullptr;         // second spectrum (FSC), owned
+    double *fsc_sums = nullptr;    // [3][n_shells], owned
+    int fsc_cap = 0;
     double *auto_stats = nullptr;  // automatic stopping: [iteration][64 slots][2], owned
     double *auto_delta = nullptr;  // [iteration]
     int auto_cap = 0;
@@ -571,6 +574,8 @@ extern "C" cubic_status_t cubic_rl_plan_destroy(cubic_rl_plan_t plan)
     cudaFree(plan->stage_out);
     cudaFree(plan->bwd);
     cudaFree(plan->Hr);
+    cudaFree(plan->ws2);
+    cudaFree(plan->fsc_sums);
     cudaFree(plan->auto_stats);
     cudaFree(plan->auto_delta);
     for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
@@ -1533,6 +1538,93 @@ extern "C" cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const f
         CUBIC_CUDA(cudaMemcpyAsync(history, p->auto_delta, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, st));
         CUBIC_CUDA(cudaStreamSynchronize(st));
     }
+    return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ Fourier Shell Correlation
+//
+// FSC(s) = Re sum A conj B / sqrt(sum |A|^2 sum |B|^2) over the frequencies of shell s,
+// the paper's resolution metric (FRC/FSC, Sections 3 and 4).  Shells are uniform in the
+// normalised radius rho = |(kz/nz, ky/ny, kx/nx)| (signed frequencies) up to Nyquist:
+// s = floor(2 S rho), rho >= 1/2 left out.  rho^2 = rn / den is rational, so the shell is
+// decided exactly in integers.  The half spectrum stands for the full one: columns
+// 0 < kx < nx/2 count twice (their mirror -kx has the same shell and conjugate values).
+
+constexpr int kFscMaxShells = 1024;
+
+__global__ void __launch_bounds__(256) k_fsc_bins(const float2 *__restrict__ A, const float2 *__restrict__ B,
+                                                  int64_t nz, int64_t ny, int64_t nx, int64_t xh, int64_t xp,
+                                                  int S, double *__restrict__ sums)
+{
+    extern __shared__ float sh_fsc[];  // [3][S]
+    for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) sh_fsc[i] = 0.f;
+    __syncthreads();
+    const int64_t cA = ny * ny * nx * nx, cB = nz * nz * nx * nx, cC = nz * nz * ny * ny;
+    const __int128 den = (__int128)cA * nz * nz;
+    const __int128 S4 = (__int128)4 * S * S;
+    const int64_t n = nz * ny * xh;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t kx = i % xh, row = i / xh, y = row % ny, z = row / ny;
+        const int64_t kz = 2 * z > nz ? z - nz : z, ky = 2 * y > ny ? y - ny : y;
+        const int64_t rn = kz * kz * cA + ky * ky * cB + kx * kx * cC;
+        const __int128 t = S4 * rn;  // shell s iff s^2 den <= t < (s+1)^2 den
+        if (t >= den * S * S) continue;  // rho >= 1/2
+        int sh = (int)(2.f * (float)S * sqrtf((float)rn / (float)den));  // estimate, corrected below
+        if (sh > S - 1) sh = S - 1;
+        while (sh > 0 && (__int128)sh * sh * den > t) --sh;
+        while (sh + 1 < S && (__int128)(sh + 1) * (sh + 1) * den <= t) ++sh;
+        const float w = (kx == 0 || 2 * kx == nx) ? 1.f : 2.f;
+        const float2 a = A[row * xp + kx], b = B[row * xp + kx];
+        atomicAdd(&sh_fsc[sh], w * (a.x * b.x + a.y * b.y));
+        atomicAdd(&sh_fsc[S + sh], w * (a.x * a.x + a.y * a.y));
+        atomicAdd(&sh_fsc[2 * S + sh], w * (b.x * b.x + b.y * b.y));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * S; i += blockDim.x)
+        if (sh_fsc[i] != 0.f) atomicAdd(&sums[i], (double)sh_fsc[i]);
+}
+
+__global__ void k_fsc_final(const double *__restrict__ sums, int S, float *__restrict__ fsc)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+        const double d = sqrt(sums[S + s] * sums[2 * S + s]);
+        fsc[s] = d > 0.0 ? (float)(sums[s] / d) : 0.f;
+    }
+}
+
+extern "C" cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const float *b, int n_shells, float *fsc,
+                                    void *stream)
+{
+    if (!plan || !a || !b || !fsc) return fail(CUBIC_ERR_INVALID_ARG, "plan, a, b and fsc must be non-null");
+    if (n_shells < 1 || n_shells > kFscMaxShells)
+        return fail(CUBIC_ERR_INVALID_ARG, "n_shells must be in [1, %d]", kFscMaxShells);
+    if (!aligned16(a) || !aligned16(b)) return fail(CUBIC_ERR_ALIGNMENT, "a and b must be 16-byte aligned");
+    cubic_rl_plan_s *p = plan;
+    cubic_status_t s = ensure_workspace(p);
+    if (s != CUBIC_OK) return s;
+    if (!p->ws2) {
+        void *m = nullptr;
+        CUBIC_CUDA(cudaMalloc(&m, spec_elems(p) * sizeof(float2)));
+        p->ws2 = (float2 *)m;
+    }
+    if (p->fsc_cap < n_shells) {
+        cudaDeviceSynchronize();
+        cudaFree(p->fsc_sums);
+        p->fsc_sums = nullptr;
+        p->fsc_cap = 0;
+        void *m = nullptr;
+        CUBIC_CUDA(cudaMalloc(&m, 3 * (size_t)kFscMaxShells * sizeof(double)));
+        p->fsc_sums = (double *)m;
+        p->fsc_cap = kFscMaxShells;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = enqueue_forward3(p, a, p->ws, 1.f, st)) != CUBIC_OK) return s;
+    if ((s = enqueue_forward3(p, b, p->ws2, 1.f, st)) != CUBIC_OK) return s;
+    CUBIC_CUDA(cudaMemsetAsync(p->fsc_sums, 0, 3 * (size_t)n_shells * sizeof(double), st));
+    k_fsc_bins<<<grid_for(p->rows * p->xh, 256, 152 * 8), 256, 3 * n_shells * sizeof(float), st>>>(
+        p->ws, p->ws2, p->nz, p->ny, p->nx, p->xh, p->xp, n_shells, p->fsc_sums);
+    k_fsc_final<<<(n_shells + 255) / 256, 256, 0, st>>>(p->fsc_sums, n_shells, fsc);
+    CUBIC_CUDA(cudaGetLastError());
     return CUBIC_OK;
 }
 
