@@ -103,18 +103,25 @@ constexpr size_t col_tile_bytes()
     return (size_t)N * B * sizeof(float2);
 }
 
-template <int N, int P, int B, int KIND, int NS = 2>
+// H stage of the Z pass: a complex tile, or half of it for a real H (HREAL)
+template <int N, int B, int P, bool HREAL>
+constexpr size_t col_hstage_bytes()
+{
+    return HREAL ? ((size_t)N * B * sizeof(float) + 1023) / 1024 * 1024 : col_stage_bytes<N, B, P>();
+}
+
+template <int N, int P, int B, int KIND, int NS = 2, bool HREAL = false>
 constexpr size_t col_smem_bytes()
 {
     // 1 KB for the barriers (keeps the stages 1 KB aligned), NS data stages,
     // NS H stages for the Z pass, then the stage twiddle table
-    return 1024 + NS * col_stage_bytes<N, B, P>() * (KIND == COL_Z ? 2 : 1) +
+    return 1024 + NS * (col_stage_bytes<N, B, P>() + (KIND == COL_Z ? col_hstage_bytes<N, B, P, HREAL>() : 0)) +
            (size_t)tw_table_size(N, N / P) * sizeof(float2);
 }
 
 // NS shared-memory stages; tiles are prefetched D = max(1, NS - 2) ahead, so up to
 // NS - D - 1 tile stores may still be draining when a stage is refilled.
-template <int N, int P, int B, int KIND, int NS = 2>
+template <int N, int P, int B, int KIND, int NS = 2, bool HREAL = false>
 __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CUtensorMap tm_spec,
                                                       const __grid_constant__ CUtensorMap tm_h, ColArgs a)
 {
@@ -127,13 +134,17 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
     constexpr size_t SB = col_stage_bytes<N, B, P>();
     extern __shared__ __align__(1024) unsigned char smem_col[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_col);  // full[0 .. NS)
+    constexpr size_t HB = col_hstage_bytes<N, B, P, HREAL>();
     auto stage = [&](int s) { return reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)s * SB); };
-    auto hstage = [&](int s) { return reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)(NS + s) * SB); };
-    const bool realH = (KIND == COL_Z) && a.mode == ZM_MUL_REAL;
-    const bool needH = (KIND == COL_Z) && (a.mode == ZM_CONV || a.mode == ZM_CORR || realH);
+    auto hstage = [&](int s) {
+        return reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)NS * SB + (size_t)s * HB);
+    };
+    // a real H needs the HREAL instantiation (its H stages are half size)
+    const bool realH = HREAL && (KIND == COL_Z) && a.mode == ZM_MUL_REAL;
+    const bool needH = (KIND == COL_Z) && (HREAL ? realH : (a.mode == ZM_CONV || a.mode == ZM_CORR));
     const unsigned tile_bytes = (unsigned)(col_tile_bytes<N, B>() * (needH ? (realH ? 3 : 4) : 2) / 2);
     using FFT = LineFFT<N, P, true>;
-    float2 *stw = reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)NS * SB * (KIND == COL_Z ? 2 : 1));
+    float2 *stw = reinterpret_cast<float2 *>(smem_col + 1024 + (size_t)NS * (SB + (KIND == COL_Z ? HB : 0)));
 
     const int b = threadIdx.x % B;
     const int t = threadIdx.x / B;

@@ -155,28 +155,28 @@ inline cudaError_t encode_spectrum_map(CUtensorMap *tm, const void *base, int64_
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int N, int P, int B, int KIND, int NS>
+template <int N, int P, int B, int KIND, int NS, bool HREAL>
 int col_grid_cap()
 {
     static int cap = [] {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colpass_tma<N, P, B, KIND, NS>, P * B,
-                                                      col_smem_bytes<N, P, B, KIND, NS>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colpass_tma<N, P, B, KIND, NS, HREAL>, P * B,
+                                                      col_smem_bytes<N, P, B, KIND, NS, HREAL>());
         return (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
     }();
     return cap;
 }
 
-template <int N, int P, int B, int KIND, int NS>
+template <int N, int P, int B, int KIND, int NS, bool HREAL = false>
 cudaError_t launch_col(const float2 *spec, const float2 *H, const float *Hr, int64_t nz, int64_t ny, int64_t xp,
                        int64_t col0, int64_t col1, int64_t outer, const float2 *tw, int mode, float scale,
                        unsigned *err, cudaStream_t st)
 {
     constexpr int R = box_rows(N);
-    constexpr size_t smem = col_smem_bytes<N, P, B, KIND, NS>();
-    auto fn = k_colpass_tma<N, P, B, KIND, NS>;
+    constexpr size_t smem = col_smem_bytes<N, P, B, KIND, NS, HREAL>();
+    auto fn = k_colpass_tma<N, P, B, KIND, NS, HREAL>;
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (col0 % B != 0) return cudaErrorInvalidValue;
@@ -211,7 +211,7 @@ cudaError_t launch_col(const float2 *spec, const float2 *H, const float *Hr, int
     c.scale = scale;
     c.err = err;
     if (c.ntiles == 0) return cudaSuccess;
-    const int64_t cap = col_grid_cap<N, P, B, KIND, NS>();
+    const int64_t cap = col_grid_cap<N, P, B, KIND, NS, HREAL>();
     const unsigned grid = (unsigned)(c.ntiles < cap ? c.ntiles : cap);
     return launch_pdl(fn, dim3(grid), dim3(P * B), smem, st, tm_spec, tm_h, c);
 }
@@ -227,6 +227,9 @@ template <int N, int P, int B, int NS>
 cudaError_t launch_z_tma(const ZArgs &a, cudaStream_t st)
 {
     const bool needH = a.mode == ZM_CONV || a.mode == ZM_CORR;
+    if (a.mode == ZM_MUL_REAL)
+        return launch_col<N, P, B, COL_Z, NS, true>(a.spec, nullptr, a.Hr, N, a.ny, a.xp, a.col0, a.col1, a.ny,
+                                                    a.tw, a.mode, a.scale, a.err, st);
     return launch_col<N, P, B, COL_Z, NS>(a.spec, needH ? a.H : nullptr, a.Hr, N, a.ny, a.xp, a.col0, a.col1, a.ny, a.tw,
                                       a.mode, a.scale, a.err, st);
 }

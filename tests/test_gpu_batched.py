@@ -1,8 +1,10 @@
 """Batched deconvolution (many uneven volumes, one CUDA graph) against the plain path and the oracle.
 
-The batched path runs the same per-length transforms as the plain path; with the
-default launch shapes (same threads per line, hence the same radix plan) the results
-are bitwise equal, and they match the FP64 oracle within the plain path's tolerance.
+The batched path runs the same per-length transforms as the plain path, with the same
+threads per line (hence the same radix plan) but other kernels (tiles, loads): the
+results agree with the plain path to rounding (relative L2 <= 1e-6; the compiler may
+contract products into FMAs differently in different kernels), and with the FP64 oracle
+within the plain path's tolerance.
 """
 import numpy as np
 import pytest
@@ -58,7 +60,7 @@ def test_batched_equals_plain_calls(cr):
         ref = torch.empty_like(img)
         cr.cubic_rl_deconvolve(plan, img, n_iter, 1e-6, ref)
         torch.cuda.synchronize()
-        assert torch.equal(out, ref)
+        assert rel_l2(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-6
 
 
 def test_batched_matches_oracle_and_replays(cr):
