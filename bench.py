@@ -193,7 +193,10 @@ def run_ours(args, w: synth.Workload):
     out = torch.empty_like(d)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    cr.cubic_rl_autotune(plan, d, out)          # untimed, like plan creation
+    if args.variants:   # pinned launch shapes (a profiler distorts the tuner's timings)
+        cr.cubic_rl_plan_set_variants(plan, *(int(v) for v in args.variants.split(",")))
+    else:
+        cr.cubic_rl_autotune(plan, d, out)      # untimed, like plan creation
     tune_s = time.perf_counter() - t0
     variants = cr.cubic_rl_plan_variants(plan)
 
@@ -267,7 +270,8 @@ def run_ours(args, w: synth.Workload):
                         "GBps": round(v["bytes"] / v["launches"] / (v["ms"] / v["timed"] * 1e-3) / 1e9, 1)}
                     for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["ms"])},
         "flux_rel_err": flux_rel,
-        "tuning": {"variants_xyz": list(variants[1]), "of": list(variants[0]), "seconds": round(tune_s, 2)},
+        "tuning": {"variants_xyz": list(variants[1]), "of": list(variants[0]), "seconds": round(tune_s, 2),
+                   "pinned": bool(args.variants)},
         "clocks": clk,
     }
     if not args.no_batched:
@@ -493,6 +497,8 @@ def main():
     ap.add_argument("--ncu-target", metavar="VX,VY,VZ",
                     help="profiling target only: plan + --ncu-iters RL iterations with these launch shapes")
     ap.add_argument("--ncu-iters", type=int, default=1)
+    ap.add_argument("--variants", metavar="VX,VY,VZ",
+                    help="pin the launch shapes of the timed workload instead of autotuning")
     args = ap.parse_args()
     w = synth.PLAIN[args.workload]
     if args.ncu_target:
