@@ -71,6 +71,8 @@ def _load():
                 "orc_rl_grad": ([P, P, i64, i64, i64, ci, cd, P, P, P], ci),
                 "orc_fsc": ([P, P, i64, i64, i64, ci, P, P, P, P], ci),
                 "orc_rl_auto": ([P, P, i64, i64, i64, ci, cd, cd, ci, P, ctypes.POINTER(ci), P], ci),
+                "orc_rl_accel": ([P, P, i64, i64, i64, ci, cd, P, P], ci),
+                "orc_accel_linear": ([i64, ci, P, P, P, P, P], ci),
                 "orc_psf_gaussian": ([i64, i64, i64, cd, cd, cd, P], ci),
                 "orc_psf_gaussian_grad": ([i64, i64, i64, cd, cd, cd, P, P], ci),
             }
@@ -192,6 +194,27 @@ def rl_auto(d, psf, max_iter: int, eps: float, tol: float, check_every: int = 1)
     _check(_load().orc_rl_auto(_p(dd), _p(p), *dd.shape, int(max_iter), float(eps), float(tol), int(check_every),
                                _p(out), ctypes.byref(n), _p(hist)), "rl_auto")
     return out, int(n.value), hist[:n.value].copy()
+
+
+def rl_accel(d, psf, n_iter: int, eps: float = 1e-6):
+    """Accelerated RL (Biggs-Andrews extrapolation); returns (estimate, alpha_0..alpha_{n-1})."""
+    dd, p = _f64(d), _f64(psf)
+    if dd.shape != p.shape:
+        raise ValueError("image and PSF must have the same shape")
+    out = np.empty_like(dd)
+    alpha = np.zeros(max(1, int(n_iter)), np.float64)
+    _check(_load().orc_rl_accel(_p(dd), _p(p), *dd.shape, int(n_iter), float(eps), _p(out), _p(alpha)),
+           "rl_accel")
+    return out, alpha[:int(n_iter)].copy()
+
+
+def accel_linear(xs, lam, x0, n_iter: int):
+    """The same extrapolation with the linear step psi(y) = xs + lam (y - xs); returns (x_n, alphas)."""
+    a, l, x = _f64(xs).ravel(), _f64(lam).ravel(), _f64(x0).ravel()
+    out = np.empty_like(a)
+    alpha = np.zeros(max(1, int(n_iter)), np.float64)
+    _check(_load().orc_accel_linear(a.size, int(n_iter), _p(a), _p(l), _p(x), _p(out), _p(alpha)), "accel_linear")
+    return out, alpha[:int(n_iter)].copy()
 
 
 def fsc(a, b, n_shells: int):

@@ -513,3 +513,110 @@ def test_fsc_shell_edges_exact():
         a = _tone(shape, k0)
         _, _, da, _ = oracle.fsc(a, a, 4)
         assert da[shell] > 0 and np.count_nonzero(da > 1e-9) == 1, (k0, da)
+
+
+# ------------------------------------------------------ accelerated RL (Biggs-Andrews)
+#
+# The extrapolation is pinned on a linear step psi(y) = xs + lam (y - xs), whose
+# iterates follow in closed form:
+#   - 0 < lam < 1: the moves are all parallel, alpha_k = lam^(k-1) (k >= 2), and the
+#     error after n steps is lam^(1 + n(n-1)/2) e0 (by induction on the exponents);
+#   - lam < 0: the ratio of successive changes is lam < 0, so alpha clamps to 0 and the
+#     plain iteration remains, error lam^n e0;
+#   - lam > 1: the ratio exceeds 1, alpha clamps to 1, and the error coefficient s_n
+#     follows s_{n+1} = lam (2 s_n - s_{n-1}) from s_1 = lam, s_2 = lam^2.
+# The RL composition is pinned by the cases where RL itself has a closed form.
+
+def test_accel_linear_contraction_closed_form():
+    r = np.random.default_rng(71)
+    xs = np.full(64, 5.0)
+    e0 = r.uniform(-1, 1, 64)
+    for lam in (0.3, 0.7, 0.9):
+        for n in range(1, 9):
+            x, a = oracle.accel_linear(xs, np.full(64, lam), xs + e0, n)
+            assert np.allclose(x - xs, lam ** (1 + n * (n - 1) // 2) * e0, rtol=1e-10, atol=1e-14)
+            assert np.allclose(a, [0.0, 0.0] + [lam ** (k - 1) for k in range(2, n)][:max(0, n - 2)])
+
+
+def test_accel_linear_alpha_clamps():
+    r = np.random.default_rng(72)
+    xs = np.full(32, 5.0)
+    e0 = r.uniform(-1, 1, 32)
+    # negative ratio: alpha clamps to 0, plain iteration
+    x, a = oracle.accel_linear(xs, np.full(32, -0.6), xs + e0, 7)
+    assert np.all(a == 0.0)
+    assert np.allclose(x - xs, (-0.6) ** 7 * e0, rtol=1e-12)
+    # ratio above 1: alpha clamps to 1 from k = 2 on
+    lam, n = 1.3, 8
+    x, a = oracle.accel_linear(xs, np.full(32, lam), xs + 0.01 * e0, n)
+    assert np.all(a[:2] == 0.0) and np.all(a[2:] == 1.0)
+    z1, z2 = lam + np.sqrt(lam * lam - lam), lam - np.sqrt(lam * lam - lam)
+    # s_k = A z1^k + B z2^k through s_1 = lam, s_2 = lam^2
+    A, B = np.linalg.solve([[z1, z2], [z1 ** 2, z2 ** 2]], [lam, lam ** 2])
+    assert np.allclose(x - xs, (A * z1 ** n + B * z2 ** n) * 0.01 * e0, rtol=1e-10)
+
+
+def test_accel_linear_prediction_clamped_at_zero():
+    # voxel 0 decays slowly and sets alpha near 0.9; voxel 1 decays fast, so the
+    # prediction along its last move is negative at k = 2 and is set to 0, after which
+    # psi keeps it at 0 (xs = 0) for good
+    xs = np.zeros(2)
+    lam = np.array([0.9, 0.2])
+    x0 = np.array([1.0, 0.01])
+    _, a = oracle.accel_linear(xs, lam, x0, 3)
+    assert 0.85 < a[2] < 0.95
+    unclamped = 0.2 * 0.01 * (0.2 + a[2] * 0.2 - a[2])
+    assert unclamped < 0
+    for n in (3, 4, 6):
+        x, _ = oracle.accel_linear(xs, lam, x0, n)
+        assert x[1] == 0.0 and x[0] > 0.0
+
+
+def test_rl_accel_first_two_iterates_are_plain_rl():
+    d, _ = synth.make_volume((6, 8, 10), 3, (1.0, 2.0), 5.0, 1.0, 1.5, 73)
+    psf = oracle.psf_gaussian(d.shape, 1.0, 1.5)
+    for n in (0, 1, 2):
+        x, a = oracle.rl_accel(d, psf, n, 1e-6)
+        assert np.allclose(x, oracle.rl(d, psf, n, 1e-6), rtol=1e-13, atol=0)
+        assert np.all(a == 0.0)
+
+
+def test_rl_accel_delta_and_constant_fixed_points():
+    shape = (4, 6, 5)
+    d = np.random.default_rng(74).uniform(1, 100, shape)
+    psf = np.zeros(shape)
+    psf[tuple(n // 2 for n in shape)] = 1.0
+    for n in (1, 3, 6):
+        x, a = oracle.rl_accel(d, psf, n, 1e-6)
+        assert np.allclose(x, d, rtol=1e-12)
+        assert np.all(a == 0.0)   # g_1 = 0: no move to extrapolate
+    # constant image, normalised PSF: every change is at rounding level, so whatever
+    # alpha their ratio gives, the estimate stays at the constant
+    psf = np.random.default_rng(75).uniform(size=shape)
+    psf /= psf.sum()
+    x, a = oracle.rl_accel(np.full(shape, 3.5), psf, 6, 1e-6)
+    assert np.allclose(x, 3.5, rtol=1e-12) and np.all((a >= 0) & (a <= 1))
+    # exactly zero changes (the 0/0 ratio) give alpha = 0: a linear step at its fixed point
+    x, a = oracle.accel_linear(np.full(8, 2.0), np.full(8, 0.5), np.full(8, 2.0), 5)
+    assert np.all(x == 2.0) and np.all(a == 0.0)
+
+
+def test_rl_accel_flux_nonnegativity_and_speedup():
+    d, _ = synth.workload_volume(synth.SMALL)
+    d = d.astype(np.float64)
+    psf = oracle.psf_gaussian(d.shape, 1.5, 3.0)
+    n = 20
+    x, a = oracle.rl_accel(d, psf, n, 1e-6)
+    assert x.min() >= 0.0
+    # every RL step conserves the flux of a normalised PSF, whatever point it starts from
+    assert abs(x.sum() - d.sum()) <= 1e-10 * d.sum()
+    assert np.all((a >= 0) & (a <= 1)) and a[2:].max() > 0.5
+    # the point of the method: RL maximises the Poisson likelihood, and the accelerated
+    # run gets further in n steps than plain RL in 2n
+    H = oracle.psf_spectrum(psf)
+
+    def nll(u):
+        b = oracle.convolve(H, u)
+        return float(np.sum(b - d * np.log(np.maximum(b, 1e-6))))
+
+    assert nll(x) < nll(oracle.rl(d, psf, 2 * n, 1e-6))
