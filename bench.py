@@ -274,6 +274,8 @@ def run_ours(args, w: synth.Workload):
                    "pinned": bool(args.variants)},
         "clocks": clk,
     }
+    if not args.no_accel:
+        result["accel"] = run_accel(cr, args, plan, d, n_iter, eps, ms / args.steps / n_iter)
     if not args.no_batched:
         result["batched"] = run_batched(cr, args)
     if not args.no_grad:
@@ -325,6 +327,55 @@ def run_batched(cr, args):
             "voxels": vox, "value": round(vox * n_iter / (ms_b * 1e-3) / 1e9, 3), "unit": UNIT,
             "ms": round(ms_b, 3), "graph_kernel_nodes": nodes, "plain_calls_ms": round(ms_p, 3),
             "speedup_vs_plain_calls": round(ms_p / ms_b, 3)}
+
+
+def run_accel(cr, args, plan, d, n_iter: int, eps: float, plain_ms_per_iter: float):
+    """Accelerated RL on the same volume and plan: time per iteration, and the plain-RL
+    iteration count whose Poisson likelihood the accelerated n_iter iterations reach."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = torch.empty_like(d)
+    alpha = torch.empty(n_iter, dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        cr.cubic_rl_deconvolve_accel(plan, d, n_iter, eps, out, alpha)
+    reps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        cr.cubic_rl_deconvolve_accel(plan, d, n_iter, eps, out, alpha)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+
+    # evaluation only (not part of the timed path): NLL = sum(b - d ln b), b = h * x
+    b = torch.empty_like(d)
+    d64 = d.double()
+
+    def nll(x):
+        cr.cubic_rl_convolve(plan, x, 0, b)
+        bb = b.double().clamp_min(eps)
+        return float((bb - d64 * bb.log()).sum().item())
+
+    nll_acc = nll(out)
+    plain = torch.empty_like(d)
+    match = None
+    curve = {}
+    for n in (n_iter, 2 * n_iter, 3 * n_iter, 4 * n_iter):
+        cr.cubic_rl_deconvolve(plan, d, n, eps, plain)
+        curve[n] = nll(plain)
+        if match is None and curve[n] <= nll_acc:
+            match = n
+    ms_it = ms / n_iter
+    res = {"workload": f"the same volume, {n_iter} accelerated iterations (Biggs-Andrews)",
+           "ms": round(ms, 3), "ms_per_iter": round(ms_it, 4), "plain_ms_per_iter": round(plain_ms_per_iter, 4),
+           "value": round(int(d.numel()) * n_iter / (ms * 1e-3) / 1e9, 3), "unit": "Gvoxel-iter/s",
+           "alpha_last": round(float(alpha[-1].item()), 4),
+           "poisson_nll": {"accel": nll_acc, **{f"plain_{n}": v for n, v in curve.items()}},
+           "plain_iters_to_match": match if match is not None else f">{4 * n_iter}"}
+    if match is not None:
+        res["time_to_same_nll_speedup"] = round(match * plain_ms_per_iter / ms, 3)
+    return res
 
 
 def run_fwd_bwd(cr, args):
@@ -494,6 +545,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--no-grad", action="store_true", help="skip the forward+backward leg")
+    ap.add_argument("--no-accel", action="store_true", help="skip the accelerated-RL leg")
     ap.add_argument("--ncu-target", metavar="VX,VY,VZ",
                     help="profiling target only: plan + --ncu-iters RL iterations with these launch shapes")
     ap.add_argument("--ncu-iters", type=int, default=1)

@@ -183,6 +183,21 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve_noalloc(const int64_t dims[3], cons
                                                      const float *image, int n_iter, float eps,
                                                      float *out, void *stream);
 
+/* Accelerated Richardson-Lucy.  The paper (Section 2) cites the acceleration of Biggs and
+ * Andrews (Applied Optics 36(8), 1997) for RL; this is their first-order vector
+ * extrapolation.  Each RL step starts from a prediction along the last move:
+ *   y_k = max(x_k + alpha_k (x_k - x_{k-1}), 0),  x_{k+1} = one RL iteration from y_k,
+ *   g_k = x_{k+1} - y_k,  alpha_{k+1} = <g_k, g_{k-1}> / <g_{k-1}, g_{k-1}> clamped to [0, 1],
+ * with x_0 = max(mean(image), eps), alpha_0 = alpha_1 = 0 and alpha = 0 for a zero
+ * denominator.  The dot products are compensated float32 sums.  out receives x_{n_iter}.
+ * alpha (device float[n_iter], may be NULL) receives alpha_0 .. alpha_{n_iter-1}.
+ * image, out: device float32 [nz][ny][nx], 16-byte aligned, not overlapping.  The first
+ * call allocates five volumes of plan-owned buffers.  Asynchronous on stream (alpha stays
+ * on the device).  Errors: INVALID_ARG (null pointers, n_iter < 0, eps <= 0 or not finite,
+ * overlap), ALIGNMENT, OUT_OF_MEMORY, CUDA. */
+CUBIC_API cubic_status_t cubic_rl_deconvolve_accel(cubic_rl_plan_t plan, const float *image, int n_iter,
+                                                   float eps, float *out, float *alpha, void *stream);
+
 /* Richardson-Lucy with automatic stopping.  The paper (Section 4) stops the iteration when
  * the improvement between consecutive iterations falls under a threshold; it names neither
  * the measure nor the threshold.  Reading taken here: the improvement of iteration k is the

@@ -65,6 +65,7 @@ _SIGS = {
     "cubic_fsc": ([_vp, _vp, _vp, _ci, _vp, _vp], _ci),
     "cubic_rl_deconvolve_auto": ([_vp, _vp, _ci, _cf, _cf, _ci, _vp, ctypes.POINTER(_ci),
                                   ctypes.POINTER(ctypes.c_double), _vp], _ci),
+    "cubic_rl_deconvolve_accel": ([_vp, _vp, _ci, _cf, _vp, _vp, _vp], _ci),
     "cubic_rl_deconvolve_ckpt": ([_vp, _vp, _ci, _cf, _ci, _vp, _vp, _vp], _ci),
     "cubic_rl_backward_workspace_bytes": ([_vp, _ci, ctypes.POINTER(_sz)], _ci),
     "cubic_rl_backward": ([_vp, _vp, _ci, _cf, _ci, _vp, _vp, _vp, _vp, _ci, _vp], _ci),
@@ -304,6 +305,15 @@ def cubic_rl_deconvolve_auto(plan: Plan, image, max_iter: int, eps: float, tol: 
                                           _ptr(out, torch.float32, plan.voxels, "out"), ctypes.byref(n), hist,
                                           _stream(stream)), "cubic_rl_deconvolve_auto")
     return int(n.value), list(hist[:n.value])
+
+
+def cubic_rl_deconvolve_accel(plan: Plan, image, n_iter: int, eps: float, out, alpha=None, stream=None) -> None:
+    """Accelerated RL (Biggs-Andrews extrapolation); alpha: optional float32 CUDA tensor of n_iter."""
+    import torch
+    a = None if alpha is None else _ptr(alpha, torch.float32, int(n_iter) if n_iter > 0 else None, "alpha")
+    _check(lib().cubic_rl_deconvolve_accel(plan.handle, _ptr(image, torch.float32, plan.voxels, "image"),
+                                           int(n_iter), float(eps), _ptr(out, torch.float32, plan.voxels, "out"),
+                                           a, _stream(stream)), "cubic_rl_deconvolve_accel")
 
 
 def cubic_fsc(plan: Plan, a, b, n_shells: int, fsc=None, stream=None):

@@ -189,12 +189,13 @@ static unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 32)
 
 enum KernelKind : int {
     KK_SUM = 0, KK_FILL, KK_SHIFT, KK_X_FWD, KK_X_INV, KK_X_RATIO, KK_X_UPDATE, KK_X_FINAL,
-    KK_Y_FWD, KK_Y_INV, KK_Z_FWD, KK_Z_INV, KK_Z_CONV, KK_Z_CORR, KK_COUNT
+    KK_Y_FWD, KK_Y_INV, KK_Z_FWD, KK_Z_INV, KK_Z_CONV, KK_Z_CORR,
+    KK_X_ACC_UPDATE, KK_X_ACC_PREDICT, KK_ACC_ALPHA, KK_COUNT
 };
 
 static const char *const kKindNames[KK_COUNT] = {
     "sum", "fill_initial", "center_to_origin", "x_fwd", "x_inv", "x_ratio", "x_update", "x_final",
-    "y_fwd", "y_inv", "z_fwd", "z_inv", "z_conv", "z_corr"};
+    "y_fwd", "y_inv", "z_fwd", "z_inv", "z_conv", "z_corr", "x_acc_update", "x_acc_predict", "acc_alpha"};
 
 // ------------------------------------------------------------------ plan
 
@@ -216,11 +217,16 @@ struct cubic_rl_plan_s {
     size_t bwd_bytes = 0;
     // point-symmetric PSF: H is real and the Z passes read it as float (half the bytes)
     float2 *ws2 = nullptr;         // second spectrum (FSC), owned
-    double *fsc_sums = nullptr;    // [3][n_shells], owned
+    float *fsc_sums = nullptr;     // [2][3][n_shells] compensated pairs, owned
     int fsc_cap = 0;
-    double *auto_stats = nullptr;  // automatic stopping: [iteration][64 slots][2], owned
-    double *auto_delta = nullptr;  // [iteration]
+    float *auto_stats = nullptr;  // automatic stopping: [iteration][64 slots][2 sums][hi, lo], owned
+    float *auto_delta = nullptr;  // [iteration]
     int auto_cap = 0;
+    // accelerated RL: x (two), y, g (two) volumes, the update pass's per-CTA partial
+    // sums and the state (den_{k-1}, alpha_{k+1}); allocated on first use, owned
+    float *acc = nullptr;
+    float4 *acc_part = nullptr;
+    float *acc_state = nullptr;
     bool allow_real_h = false;  // set by cubic_rl_plan (may allocate Hr)
     bool use_real_h = false;
     float *Hr = nullptr;        // [nz][ny][xp], owned
@@ -263,6 +269,9 @@ static double kind_bytes(const cubic_rl_plan_s *p, int kind)
     case KK_X_FINAL: return spec + 2 * real;
     case KK_Y_FWD: case KK_Y_INV: case KK_Z_FWD: case KK_Z_INV: return 2 * spec;
     case KK_Z_CONV: case KK_Z_CORR: return 3 * spec;
+    case KK_X_ACC_UPDATE: return spec + 4 * real;
+    case KK_X_ACC_PREDICT: return 3 * real + spec;
+    case KK_ACC_ALPHA: return 0.0;
     }
     return 0.0;
 }
@@ -294,6 +303,12 @@ static const int kXKind[XM_COUNT] = {KK_X_FWD, KK_X_INV, KK_X_RATIO, KK_X_UPDATE
 static cudaError_t run_x(cubic_rl_plan_s *p, int mode, const XArgs &a, cudaStream_t st)
 {
     return counted(p, kXKind[mode], st, [&] { return p->kx->xv[p->vx].fn[mode](a, st); });
+}
+
+// an X pass counted under another kind (the accelerated-RL forms of XM_FWD / XM_FINAL)
+static cudaError_t run_x_as(cubic_rl_plan_s *p, int mode, int kind, const XArgs &a, double bytes, cudaStream_t st)
+{
+    return counted(p, kind, st, [&] { return p->kx->xv[p->vx].fn[mode](a, st); }, bytes);
 }
 
 static cudaError_t run_y(cubic_rl_plan_s *p, const YArgs &a, cudaStream_t st)
@@ -578,6 +593,7 @@ extern "C" cubic_status_t cubic_rl_plan_destroy(cubic_rl_plan_t plan)
     cudaFree(plan->fsc_sums);
     cudaFree(plan->auto_stats);
     cudaFree(plan->auto_delta);
+    cudaFree(plan->acc);
     for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
     delete plan;
     return CUBIC_OK;
@@ -1072,12 +1088,41 @@ __global__ void k_add(float *__restrict__ a, const float *__restrict__ b, int64_
         a[i] += b[i];
 }
 
-// dbar += sum(g) / V where mean(d) > eps (u0 = max(mean(d), eps))
-__global__ void k_add_mean_grad(float *__restrict__ dbar, const double *__restrict__ sum_g,
+// Compensated float32 sum of x over V elements: block partials (CFloat) ...
+__global__ void __launch_bounds__(kReduceThreads) k_csum_partial(const float *__restrict__ x, int64_t V,
+                                                                 CFloat *__restrict__ partial)
+{
+    __shared__ CFloat sh[kReduceThreads / 32];
+    CFloat s{0.f, 0.f};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x)
+        s = cf_add(s, x[i]);
+    for (int o = 16; o > 0; o >>= 1)
+        s = cf_merge(s, CFloat{__shfl_down_sync(0xffffffffu, s.s, o), __shfl_down_sync(0xffffffffu, s.c, o)});
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        CFloat t{0.f, 0.f};
+        for (int w = 0; w < kReduceThreads / 32; ++w) t = cf_merge(t, sh[w]);
+        partial[blockIdx.x] = t;
+    }
+}
+
+// ... merged in a fixed order into *out
+__global__ void k_csum_final(const CFloat *__restrict__ partial, int n, float *__restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    CFloat t{0.f, 0.f};
+    for (int i = 0; i < n; ++i) t = cf_merge(t, partial[i]);
+    out[0] = t.s - t.c;
+}
+
+// dbar += sum(g) / V where mean(d) > eps (u0 = max(mean(d), eps)); sum_d is the
+// FP64 flux sum of the image, sum_g a compensated float32 sum
+__global__ void k_add_mean_grad(float *__restrict__ dbar, const float *__restrict__ sum_g,
                                 const double *__restrict__ sum_d, int64_t V, float eps)
 {
     const bool pass = sum_d[0] / (double)V > (double)eps;
-    const float add = pass ? (float)(sum_g[0] / (double)V) : 0.f;
+    const float add = pass ? sum_g[0] / (float)V : 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x)
         dbar[i] += add;
 }
@@ -1297,11 +1342,15 @@ extern "C" cubic_status_t cubic_rl_backward(cubic_rl_plan_t plan, const float *i
     }
     // the initial estimate u0 = max(mean(d), eps) depends on d
     if (grad_image) {
-        k_sum_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(g, V, p->partial);
-        k_sum_final<<<1, kReduceThreads, 0, st>>>(p->partial, kReduceBlocks, p->partial + kReduceBlocks);
+        // the plan's reduction scratch holds kReduceBlocks + 1 doubles: as CFloat partials
+        // (8 bytes each) plus one float result
+        CFloat *gpart = reinterpret_cast<CFloat *>(p->partial);
+        float *gsum = reinterpret_cast<float *>(gpart + kReduceBlocks);
+        k_csum_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(g, V, gpart);
+        k_csum_final<<<1, 32, 0, st>>>(gpart, kReduceBlocks, gsum);
         k_sum_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(image, V, red);
         k_sum_final<<<1, kReduceThreads, 0, st>>>(red, kReduceBlocks, red + kReduceBlocks);
-        k_add_mean_grad<<<gr, 256, 0, st>>>(dbar, p->partial + kReduceBlocks, red + kReduceBlocks, V, eps);
+        k_add_mean_grad<<<gr, 256, 0, st>>>(dbar, gsum, red + kReduceBlocks, V, eps);
         CUBIC_CUDA(cudaMemcpyAsync(grad_image, dbar, (size_t)V * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
     if (grad_psf) {
@@ -1320,29 +1369,6 @@ extern "C" cubic_status_t cubic_rl_backward(cubic_rl_plan_t plan, const float *i
 //   dL/dsz  = A/S (Pz - P Sz / S)             (same with dz^2 / sz^3)
 // Six sums: S (the PSF's flux) in double; the five others in compensated float
 // (a Kahan running sum per thread, error-free TwoSum merges across threads).
-
-struct CFloat {
-    float s, c;  // value = s - c (c: Kahan compensation, the negated lost low part)
-};
-
-__device__ __forceinline__ CFloat cf_add(CFloat a, float x)
-{
-    const float y = x - a.c;
-    const float t = a.s + y;
-    a.c = (t - a.s) - y;
-    a.s = t;
-    return a;
-}
-
-__device__ __forceinline__ CFloat cf_merge(CFloat a, CFloat b)
-{
-    // TwoSum of the leading parts (s + err == a.s + b.s exactly), then the tails:
-    // value = s + err - a.c - b.c
-    const float s = a.s + b.s;
-    const float bb = s - a.s;
-    const float err = (a.s - (s - bb)) + (b.s - bb);
-    return CFloat{s, a.c + b.c - err};
-}
 
 __global__ void __launch_bounds__(kReduceThreads) k_psf_gauss_grad(const float *__restrict__ gp, int64_t nz,
                                                                    int64_t ny, int64_t nx, float a_xy, float a_z,
@@ -1456,24 +1482,21 @@ extern "C" cubic_status_t cubic_psf_gaussian_backward(const int64_t dims[3], flo
 // between consecutive iterations falls under a threshold.  Here the improvement of
 // iteration k is the relative change of the estimate,
 //   delta_k = ||u_{k+1} - u_k||_2 / ||u_k||_2,
-// whose two sums the update pass accumulates as it writes u_{k+1}.  Every check_every
-// iterations (and after the last) the host reads delta and stops below the threshold.
+// whose two sums the update pass accumulates, in compensated float32, as it writes
+// u_{k+1}.  Every check_every iterations (and after the last) the host reads delta and
+// stops below the threshold.
 
-__global__ void k_delta(const double *__restrict__ slots, double *__restrict__ delta)
+// merges the 64 compensated slots of one iteration in a fixed order
+__global__ void k_delta(const float *__restrict__ slots, float *__restrict__ delta)
 {
-    __shared__ double num[64], den[64];
-    const int i = threadIdx.x;
-    num[i] = slots[2 * i];
-    den[i] = slots[2 * i + 1];
-    __syncthreads();
-    for (int w = 32; w > 0; w >>= 1) {
-        if (i < w) {
-            num[i] += num[i + w];
-            den[i] += den[i + w];
-        }
-        __syncthreads();
+    if (threadIdx.x != 0) return;
+    CFloat num{0.f, 0.f}, den{0.f, 0.f};
+    for (int i = 0; i < 64; ++i) {
+        num = cf_merge(num, CFloat{slots[4 * i], -slots[4 * i + 1]});
+        den = cf_merge(den, CFloat{slots[4 * i + 2], -slots[4 * i + 3]});
     }
-    if (i == 0) delta[0] = den[0] > 0.0 ? sqrt(num[0] / den[0]) : 0.0;
+    const float n = num.s - num.c, d = den.s - den.c;
+    delta[0] = d > 0.f ? sqrtf(n / d) : 0.f;
 }
 
 extern "C" cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const float *image, int max_iter, float eps,
@@ -1497,14 +1520,14 @@ extern "C" cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const f
         p->auto_delta = nullptr;
         p->auto_cap = 0;
         void *a = nullptr, *b = nullptr;
-        CUBIC_CUDA(cudaMalloc(&a, (size_t)max_iter * 128 * sizeof(double)));
-        p->auto_stats = (double *)a;
-        CUBIC_CUDA(cudaMalloc(&b, (size_t)max_iter * sizeof(double)));
-        p->auto_delta = (double *)b;
+        CUBIC_CUDA(cudaMalloc(&a, (size_t)max_iter * 256 * sizeof(float)));
+        p->auto_stats = (float *)a;
+        CUBIC_CUDA(cudaMalloc(&b, (size_t)max_iter * sizeof(float)));
+        p->auto_delta = (float *)b;
         p->auto_cap = max_iter;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    CUBIC_CUDA(cudaMemsetAsync(p->auto_stats, 0, (size_t)max_iter * 128 * sizeof(double), st));
+    CUBIC_CUDA(cudaMemsetAsync(p->auto_stats, 0, (size_t)max_iter * 256 * sizeof(float), st));
     if ((s = enqueue_init(p, image, eps, out, st)) != CUBIC_OK) return s;
     XArgs xa = x_args(p);
     xa.spec_in = p->ws;
@@ -1521,22 +1544,156 @@ extern "C" cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const f
         CUBIC_CUDA(run_x(p, XM_RATIO, xa, st));
         if ((s = enqueue_yzy(p, p->ws, ZM_CORR, st)) != CUBIC_OK) return s;
         XArgs xs = xa;
-        xs.stats = p->auto_stats + (size_t)k * 128;
+        xs.stats = p->auto_stats + (size_t)k * 256;
         CUBIC_CUDA(run_x(p, k + 1 < max_iter ? XM_UPDATE : XM_FINAL, xs, st));
         k_delta<<<1, 64, 0, st>>>(xs.stats, p->auto_delta + k);
         CUBIC_CUDA(cudaGetLastError());
         ++k;
         if (k % check_every == 0 || k == max_iter) {
-            double delta = 0.0;
-            CUBIC_CUDA(cudaMemcpyAsync(&delta, p->auto_delta + k - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+            float delta = 0.f;
+            CUBIC_CUDA(cudaMemcpyAsync(&delta, p->auto_delta + k - 1, sizeof(float), cudaMemcpyDeviceToHost, st));
             CUBIC_CUDA(cudaStreamSynchronize(st));
-            if (delta < (double)tol) break;  // out already holds u_k (the update wrote it)
+            if (delta < tol) break;  // out already holds u_k (the update wrote it)
         }
     }
     *n_done = k;
     if (history) {
-        CUBIC_CUDA(cudaMemcpyAsync(history, p->auto_delta, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        std::vector<float> h((size_t)k);
+        CUBIC_CUDA(cudaMemcpyAsync(h.data(), p->auto_delta, (size_t)k * sizeof(float), cudaMemcpyDeviceToHost, st));
         CUBIC_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < k; ++i) history[i] = (double)h[(size_t)i];
+    }
+    return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ accelerated RL
+//
+// Biggs-Andrews first-order vector extrapolation (the acceleration the paper cites for
+// Richardson-Lucy): every RL step starts from a prediction along the last move,
+//   y_k = max(x_k + alpha_k (x_k - x_{k-1}), 0),   x_{k+1} = RL step from y_k,
+//   g_k = x_{k+1} - y_k,   alpha_{k+1} = <g_k, g_{k-1}> / <g_{k-1}, g_{k-1}> clamped to [0, 1],
+// alpha_0 = alpha_1 = 0, and alpha = 0 for a zero denominator.  Per iteration:
+//   the usual passes up to the back-correlation's spectrum; then
+//   XM_FINAL (accelerated): x_{k+1} = y_k q, g_k, per-CTA partial sums of the two products;
+//   k_acc_alpha: the partials merged in a fixed order, alpha_{k+1} on the device;
+//   XM_FWD (accelerated): y_{k+1} from x_{k+1}, x_k, alpha, stored and transformed.
+// No host synchronisation: alpha stays on the device.
+
+// state[0] = <g_{k-1}, g_{k-1}> (from the previous call), state[1] = alpha_{k+1}
+__global__ void __launch_bounds__(1024) k_acc_alpha(const float4 *__restrict__ part, int64_t nblocks, int k,
+                                                    float *__restrict__ state, float *__restrict__ alpha_hist,
+                                                    int n_iter)
+{
+    __shared__ CFloat sn[1024], sd[1024];
+    CFloat num{0.f, 0.f}, den{0.f, 0.f};
+    for (int64_t i = threadIdx.x; i < nblocks; i += blockDim.x) {
+        const float4 q = part[i];
+        num = cf_merge(num, CFloat{q.x, q.y});
+        den = cf_merge(den, CFloat{q.z, q.w});
+    }
+    sn[threadIdx.x] = num;
+    sd[threadIdx.x] = den;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sn[threadIdx.x] = cf_merge(sn[threadIdx.x], sn[threadIdx.x + w]);
+            sd[threadIdx.x] = cf_merge(sd[threadIdx.x], sd[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float nk = sn[0].s - sn[0].c, dk = sd[0].s - sd[0].c;
+        const float dprev = state[0];
+        float al = 0.f;
+        if (k >= 1 && dprev > 0.f) {
+            const float r = nk / dprev;
+            al = r > 0.f ? (r < 1.f ? r : 1.f) : 0.f;  // also maps NaN to 0
+        }
+        state[0] = dk;
+        state[1] = al;
+        if (alpha_hist && k + 1 < n_iter) alpha_hist[k + 1] = al;
+    }
+}
+
+static cubic_status_t ensure_accel(cubic_rl_plan_s *p)
+{
+    if (p->acc) return CUBIC_OK;
+    const size_t vol = ((size_t)p->V * sizeof(float) + 255) / 256 * 256;
+    const size_t nb = (size_t)((p->rows + 1) / 2);  // most X blocks: one line pair each
+    const size_t part = (nb * sizeof(float4) + 255) / 256 * 256;
+    void *m = nullptr;
+    if (cudaMalloc(&m, 5 * vol + part + 256) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CUBIC_ERR_OUT_OF_MEMORY, "accelerated RL buffers (%zu bytes)", 5 * vol + part + 256);
+    }
+    p->acc = (float *)m;
+    p->acc_part = (float4 *)((unsigned char *)m + 5 * vol);
+    p->acc_state = (float *)((unsigned char *)m + 5 * vol + part);
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_rl_deconvolve_accel(cubic_rl_plan_t plan, const float *image, int n_iter, float eps,
+                                                    float *out, float *alpha, void *stream)
+{
+    if (!plan || !image || !out) return fail(CUBIC_ERR_INVALID_ARG, "plan, image and out must be non-null");
+    if (n_iter < 0) return fail(CUBIC_ERR_INVALID_ARG, "n_iter must be >= 0");
+    if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
+    if (!aligned16(image) || !aligned16(out)) return fail(CUBIC_ERR_ALIGNMENT, "image and out must be 16-byte aligned");
+    if (overlaps(image, out, (size_t)plan->V * sizeof(float)))
+        return fail(CUBIC_ERR_INVALID_ARG, "out must not overlap image");
+    if (alpha && ((uintptr_t)alpha % sizeof(float)) != 0) return fail(CUBIC_ERR_ALIGNMENT, "alpha must be 4-byte aligned");
+    cubic_rl_plan_s *p = plan;
+    cubic_status_t s = ensure_workspace(p);
+    if (s != CUBIC_OK) return s;
+    if ((s = ensure_accel(p)) != CUBIC_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t vol = ((size_t)p->V * sizeof(float) + 255) / 256 * 256 / sizeof(float);
+    float *xc = p->acc, *xn = p->acc + vol, *y = p->acc + 2 * vol, *gc = p->acc + 3 * vol, *gn = p->acc + 4 * vol;
+
+    if ((s = enqueue_init(p, image, eps, xc, st)) != CUBIC_OK) return s;  // x_0 = max(mean(d), eps)
+    if (n_iter == 0) {
+        CUBIC_CUDA(cudaMemcpyAsync(out, xc, (size_t)p->V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        return CUBIC_OK;
+    }
+    CUBIC_CUDA(cudaMemcpyAsync(y, xc, (size_t)p->V * sizeof(float), cudaMemcpyDeviceToDevice, st));  // y_0 = x_0
+    CUBIC_CUDA(cudaMemsetAsync(p->acc_state, 0, 2 * sizeof(float), st));
+    if (alpha) CUBIC_CUDA(cudaMemsetAsync(alpha, 0, (size_t)n_iter * sizeof(float), st));
+
+    const double spec = (double)p->rows * p->xh * 8.0, real = (double)p->V * 4.0;
+    const int64_t L = p->kx->xv[p->vx].L;
+    const int64_t nblocks = (p->rows + 2 * L - 1) / (2 * L);
+    XArgs xa = x_args(p);
+    xa.spec_in = p->ws;
+    xa.spec_out = p->ws;
+    xa.d = image;
+    xa.eps = eps;
+    xa.src = y;
+    CUBIC_CUDA(run_x(p, XM_FWD, xa, st));  // spectrum of y_0
+    for (int k = 0; k < n_iter; ++k) {
+        if ((s = enqueue_yzy(p, p->ws, ZM_CONV, st)) != CUBIC_OK) return s;  // b = h * y_k
+        CUBIC_CUDA(run_x(p, XM_RATIO, xa, st));                             // r = d / max(b, eps)
+        if ((s = enqueue_yzy(p, p->ws, ZM_CORR, st)) != CUBIC_OK) return s;  // q = h (flipped) * r
+        const bool last = k + 1 == n_iter;
+        XArgs xu = xa;                                                       // x_{k+1} = y_k q, g_k
+        xu.u = y;
+        xu.dst = last ? out : xn;
+        xu.acc_g = gn;
+        xu.acc_gprev = k >= 1 ? gc : nullptr;
+        xu.acc_part = p->acc_part;
+        CUBIC_CUDA(run_x_as(p, XM_FINAL, KK_X_ACC_UPDATE, xu, spec + (k >= 1 ? 4 : 3) * real, st));
+        if (last) break;
+        CUBIC_CUDA(counted(p, KK_ACC_ALPHA, st, [&] {
+            k_acc_alpha<<<1, 1024, 0, st>>>(p->acc_part, nblocks, k, p->acc_state, alpha, n_iter);
+            return cudaGetLastError();
+        }));
+        XArgs xq = xa;                                                       // y_{k+1}, its spectrum
+        xq.src = xn;
+        xq.acc_prev = xc;
+        xq.acc_alpha = p->acc_state + 1;
+        xq.acc_y = y;
+        CUBIC_CUDA(run_x_as(p, XM_FWD, KK_X_ACC_PREDICT, xq, 3 * real + spec, st));
+        std::swap(xc, xn);
+        std::swap(gc, gn);
     }
     return CUBIC_OK;
 }
@@ -1552,13 +1709,16 @@ extern "C" cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const f
 
 constexpr int kFscMaxShells = 1024;
 
+// Shell sums in compensated float32: per block in shared memory, then into the
+// global pairs (value = hi + lo) -- sums[0..3S) high words, sums[3S..6S) low words.
 __global__ void __launch_bounds__(256) k_fsc_bins(const float2 *__restrict__ A, const float2 *__restrict__ B,
                                                   int64_t nz, int64_t ny, int64_t nx, int64_t xh, int64_t xp,
-                                                  int S, double *__restrict__ sums)
+                                                  int S, float *__restrict__ sums)
 {
-    extern __shared__ float sh_fsc[];  // [3][S]
-    for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) sh_fsc[i] = 0.f;
+    extern __shared__ float sh_fsc[];  // [2][3][S]: high words, then low words
+    for (int i = threadIdx.x; i < 6 * S; i += blockDim.x) sh_fsc[i] = 0.f;
     __syncthreads();
+    float *lo = sh_fsc + 3 * S;
     const int64_t cA = ny * ny * nx * nx, cB = nz * nz * nx * nx, cC = nz * nz * ny * ny;
     const __int128 den = (__int128)cA * nz * nz;
     const __int128 S4 = (__int128)4 * S * S;
@@ -1575,20 +1735,24 @@ __global__ void __launch_bounds__(256) k_fsc_bins(const float2 *__restrict__ A, 
         while (sh + 1 < S && (__int128)(sh + 1) * (sh + 1) * den <= t) ++sh;
         const float w = (kx == 0 || 2 * kx == nx) ? 1.f : 2.f;
         const float2 a = A[row * xp + kx], b = B[row * xp + kx];
-        atomicAdd(&sh_fsc[sh], w * (a.x * b.x + a.y * b.y));
-        atomicAdd(&sh_fsc[S + sh], w * (a.x * a.x + a.y * a.y));
-        atomicAdd(&sh_fsc[2 * S + sh], w * (b.x * b.x + b.y * b.y));
+        catomic_add(&sh_fsc[sh], &lo[sh], w * (a.x * b.x + a.y * b.y));
+        catomic_add(&sh_fsc[S + sh], &lo[S + sh], w * (a.x * a.x + a.y * a.y));
+        catomic_add(&sh_fsc[2 * S + sh], &lo[2 * S + sh], w * (b.x * b.x + b.y * b.y));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * S; i += blockDim.x)
-        if (sh_fsc[i] != 0.f) atomicAdd(&sums[i], (double)sh_fsc[i]);
+    for (int i = threadIdx.x; i < 3 * S; i += blockDim.x) {
+        if (sh_fsc[i] != 0.f) catomic_add(&sums[i], &sums[3 * S + i], sh_fsc[i]);
+        if (lo[i] != 0.f) catomic_add(&sums[i], &sums[3 * S + i], lo[i]);
+    }
 }
 
-__global__ void k_fsc_final(const double *__restrict__ sums, int S, float *__restrict__ fsc)
+__global__ void k_fsc_final(const float *__restrict__ sums, int S, float *__restrict__ fsc)
 {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
-        const double d = sqrt(sums[S + s] * sums[2 * S + s]);
-        fsc[s] = d > 0.0 ? (float)(sums[s] / d) : 0.f;
+        const float num = sums[s] + sums[3 * S + s];
+        const float aa = sums[S + s] + sums[4 * S + s], bb = sums[2 * S + s] + sums[5 * S + s];
+        const float d = sqrtf(aa) * sqrtf(bb);  // two roots: the product of the sums may overflow
+        fsc[s] = d > 0.f ? num / d : 0.f;
     }
 }
 
@@ -1613,15 +1777,15 @@ extern "C" cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const 
         p->fsc_sums = nullptr;
         p->fsc_cap = 0;
         void *m = nullptr;
-        CUBIC_CUDA(cudaMalloc(&m, 3 * (size_t)kFscMaxShells * sizeof(double)));
-        p->fsc_sums = (double *)m;
+        CUBIC_CUDA(cudaMalloc(&m, 6 * (size_t)kFscMaxShells * sizeof(float)));
+        p->fsc_sums = (float *)m;
         p->fsc_cap = kFscMaxShells;
     }
     cudaStream_t st = (cudaStream_t)stream;
     if ((s = enqueue_forward3(p, a, p->ws, 1.f, st)) != CUBIC_OK) return s;
     if ((s = enqueue_forward3(p, b, p->ws2, 1.f, st)) != CUBIC_OK) return s;
-    CUBIC_CUDA(cudaMemsetAsync(p->fsc_sums, 0, 3 * (size_t)n_shells * sizeof(double), st));
-    k_fsc_bins<<<grid_for(p->rows * p->xh, 256, 152 * 8), 256, 3 * n_shells * sizeof(float), st>>>(
+    CUBIC_CUDA(cudaMemsetAsync(p->fsc_sums, 0, 6 * (size_t)n_shells * sizeof(float), st));
+    k_fsc_bins<<<grid_for(p->rows * p->xh, 256, 152 * 8), 256, 6 * n_shells * sizeof(float), st>>>(
         p->ws, p->ws2, p->nz, p->ny, p->nx, p->xh, p->xp, n_shells, p->fsc_sums);
     k_fsc_final<<<(n_shells + 255) / 256, 256, 0, st>>>(p->fsc_sums, n_shells, fsc);
     CUBIC_CUDA(cudaGetLastError());

@@ -20,6 +20,7 @@
 //            (correlation = convolution with the flipped PSF), inverse z FFT.
 #pragma once
 
+#include "csum.cuh"
 #include "fft_core.cuh"
 #include "tma.cuh"
 
@@ -51,9 +52,22 @@ struct XArgs {
     // store q (keep_a)
     float *keep_a;
     float *keep_b;
-    // optional (XM_UPDATE / XM_FINAL): adds sum((u_new - u)^2) and sum(u^2) into
-    // stats[2 s] and stats[2 s + 1], s = one of 64 slots (spread to avoid contention)
-    double *stats;
+    // optional (XM_UPDATE / XM_FINAL): adds sum((u_new - u)^2) into the compensated
+    // pair stats[4 s], stats[4 s + 1] (value = hi + lo) and sum(u^2) into stats[4 s + 2],
+    // stats[4 s + 3]; s is one of 64 slots (spread to avoid contention)
+    float *stats;
+    // optional, accelerated RL (null: the plain pass):
+    //  XM_FWD with acc_prev: the rows transformed are the prediction
+    //    y = max(src + alpha (src - acc_prev), 0), alpha = *acc_alpha, also stored to acc_y;
+    //  XM_FINAL with acc_g: g = out - u is stored to acc_g, and the CTA's compensated sums
+    //    of g * acc_gprev (0 where acc_gprev is null) and of g * g go to acc_part[block]
+    //    as (num.s, num.c, den.s, den.c), value = s - c.
+    const float *acc_prev;
+    const float *acc_alpha;
+    float *acc_y;
+    float *acc_g;
+    const float *acc_gprev;
+    float4 *acc_part;
 };
 
 struct YArgs {
@@ -141,6 +155,47 @@ constexpr size_t x_smem_bytes()
            (size_t)L * x_smem_line<N, P>() * sizeof(float2);
 }
 
+// Merges two compensated sums over the T threads of the CTA, in a fixed order
+// (deterministic); thread 0 receives (a.s, a.c, b.s, b.c).  Every thread must call it.
+template <int T>
+__device__ __forceinline__ float4 block_merge2(CFloat a, CFloat b)
+{
+    __shared__ CFloat red[2][T % 32 == 0 ? T / 32 : T];
+    if constexpr (T % 32 == 0) {
+        // full warps: shuffle tree, then the warps' results in order
+        for (int o = 16; o > 0; o >>= 1) {
+            a = cf_merge(a, CFloat{__shfl_down_sync(0xffffffffu, a.s, o), __shfl_down_sync(0xffffffffu, a.c, o)});
+            b = cf_merge(b, CFloat{__shfl_down_sync(0xffffffffu, b.s, o), __shfl_down_sync(0xffffffffu, b.c, o)});
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[0][threadIdx.x >> 5] = a;
+            red[1][threadIdx.x >> 5] = b;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < T / 32; ++w) {
+                a = cf_merge(a, red[0][w]);
+                b = cf_merge(b, red[1][w]);
+            }
+        }
+    } else {
+        // other widths: pairwise tree in shared memory
+        red[0][threadIdx.x] = a;
+        red[1][threadIdx.x] = b;
+        __syncthreads();
+        for (int s = 1; s < T; s *= 2) {
+            if (threadIdx.x % (2 * s) == 0 && threadIdx.x + s < T) {
+                red[0][threadIdx.x] = cf_merge(red[0][threadIdx.x], red[0][threadIdx.x + s]);
+                red[1][threadIdx.x] = cf_merge(red[1][threadIdx.x], red[1][threadIdx.x + s]);
+            }
+            __syncthreads();
+        }
+        a = red[0][0];
+        b = red[1][0];
+    }
+    return make_float4(a.s, a.c, b.s, b.c);
+}
+
 template <int N, int P, int L, int MODE>
 __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
 {
@@ -203,11 +258,28 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     float2 v[E];
     if constexpr (MODE == XM_FWD) {
         const float *s0 = a.src + r0 * N, *s1 = a.src + r1 * N;
-        static_for<0, E>([&](auto i_) {
-            constexpr int i = CUBIC_CI(i_);
-            const int n = t + P * i;
-            v[i] = make_float2(ok0 ? __ldg(s0 + n) : 0.f, ok1 ? __ldg(s1 + n) : 0.f);
-        });
+        if (a.acc_prev) {
+            // accelerated RL: extrapolate along the last move, clamp at 0, keep y
+            const float al = *a.acc_alpha;
+            const float *p0 = a.acc_prev + r0 * N, *p1 = a.acc_prev + r1 * N;
+            float *y0 = a.acc_y + r0 * N, *y1 = a.acc_y + r1 * N;
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                const int n = t + P * i;
+                const float x0 = ok0 ? __ldg(s0 + n) : 0.f, x1 = ok1 ? __ldg(s1 + n) : 0.f;
+                const float q0 = ok0 ? __ldg(p0 + n) : 0.f, q1 = ok1 ? __ldg(p1 + n) : 0.f;
+                const float w0 = fmaxf(fmaf(al, x0 - q0, x0), 0.f), w1 = fmaxf(fmaf(al, x1 - q1, x1), 0.f);
+                if (ok0) y0[n] = w0;
+                if (ok1) y1[n] = w1;
+                v[i] = make_float2(w0, w1);
+            });
+        } else {
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                const int n = t + P * i;
+                v[i] = make_float2(ok0 ? __ldg(s0 + n) : 0.f, ok1 ? __ldg(s1 + n) : 0.f);
+            });
+        }
     } else {
         const bool landed = mbar_wait_bounded(&bar[1], 0, a.err);
         if (!__syncthreads_and(landed)) return;
@@ -280,6 +352,10 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             const bool keep = a.keep_a != nullptr;
             const bool stats = a.stats != nullptr;
             float s_num = 0.f, s_den = 0.f;
+            // accelerated RL (XM_FINAL only): g = x - u and its two dot products
+            const bool acc = MODE == XM_FINAL && a.acc_g != nullptr;
+            const bool acc_prev = a.acc_gprev != nullptr;
+            CFloat c_num{0.f, 0.f}, c_den{0.f, 0.f};
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
@@ -289,6 +365,19 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
                 if (keep) {
                     if (ok0) kq0[n] = v[i].x;
                     if (ok1) kq1[n] = v[i].y;
+                }
+                if constexpr (MODE == XM_FINAL) {
+                    if (acc) {
+                        const float g0 = x0 - u0v, g1 = x1 - u1v;  // 0 on rows past the end
+                        if (ok0) a.acc_g[r0 * N + n] = g0;
+                        if (ok1) a.acc_g[r1 * N + n] = g1;
+                        if (acc_prev) {
+                            const float h0 = ok0 ? __ldg(a.acc_gprev + r0 * N + n) : 0.f;
+                            const float h1 = ok1 ? __ldg(a.acc_gprev + r1 * N + n) : 0.f;
+                            c_num = cf_add(cf_add(c_num, g0 * h0), g1 * h1);
+                        }
+                        c_den = cf_add(cf_add(c_den, g0 * g0), g1 * g1);
+                    }
                 }
                 if (stats) {
                     s_num = fmaf(x0 - u0v, x0 - u0v, fmaf(x1 - u1v, x1 - u1v, s_num));
@@ -302,18 +391,25 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
                 // warp sums where the warp is full, else one add per thread
                 const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
                 const int slot = (int)((block * ((P * L + 31) / 32) + warp) & 63);
+                float *st4 = a.stats + 4 * slot;
                 if ((warp + 1) * 32 <= P * L) {
                     for (int o = 16; o > 0; o >>= 1) {
                         s_num += __shfl_down_sync(0xffffffffu, s_num, o);
                         s_den += __shfl_down_sync(0xffffffffu, s_den, o);
                     }
                     if (lane == 0) {
-                        atomicAdd(&a.stats[2 * slot], (double)s_num);
-                        atomicAdd(&a.stats[2 * slot + 1], (double)s_den);
+                        catomic_add(st4, st4 + 1, s_num);
+                        catomic_add(st4 + 2, st4 + 3, s_den);
                     }
                 } else {
-                    atomicAdd(&a.stats[2 * slot], (double)s_num);
-                    atomicAdd(&a.stats[2 * slot + 1], (double)s_den);
+                    catomic_add(st4, st4 + 1, s_num);
+                    catomic_add(st4 + 2, st4 + 3, s_den);
+                }
+            }
+            if constexpr (MODE == XM_FINAL) {
+                if (acc) {  // uniform over the CTA
+                    const float4 tot = block_merge2<P * L>(c_num, c_den);
+                    if (threadIdx.x == 0) a.acc_part[block] = tot;
                 }
             }
         }
