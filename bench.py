@@ -340,6 +340,7 @@ def run_accel(cr, args, plan, d, n_iter: int, eps: float, plain_ms_per_iter: flo
     for _ in range(2):
         cr.cubic_rl_deconvolve_accel(plan, d, n_iter, eps, out, alpha)
     reps = max(1, min(args.steps, 5))
+    cr.cubic_rl_profile(plan, True, max_events=2 * (n_iter * 10 + 8) * reps + 64)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(reps):
@@ -347,6 +348,11 @@ def run_accel(cr, args, plan, d, n_iter: int, eps: float, plain_ms_per_iter: flo
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    prof = cr.cubic_rl_profile_read(plan)
+    cr.cubic_rl_profile(plan, False)
+    kern = {k: {"avg_us": round(v["ms"] / v["timed"] * 1e3, 2),
+                "GBps": round(v["bytes"] / v["launches"] / (v["ms"] / v["timed"] * 1e-3) / 1e9, 1)}
+            for k, v in prof.items() if v["timed"] > 0 and k.startswith(("x_acc", "acc_"))}
 
     # evaluation only (not part of the timed path): NLL = sum(b - d ln b), b = h * x
     b = torch.empty_like(d)
@@ -361,20 +367,26 @@ def run_accel(cr, args, plan, d, n_iter: int, eps: float, plain_ms_per_iter: flo
     plain = torch.empty_like(d)
     match = None
     curve = {}
-    for n in (n_iter, 2 * n_iter, 3 * n_iter, 4 * n_iter):
+    lower = n_iter
+    for n in (n_iter, 2 * n_iter, 4 * n_iter, 8 * n_iter, 16 * n_iter):   # doubling search
         cr.cubic_rl_deconvolve(plan, d, n, eps, plain)
         curve[n] = nll(plain)
-        if match is None and curve[n] <= nll_acc:
+        if curve[n] <= nll_acc:
             match = n
+            break
+        lower = n
     ms_it = ms / n_iter
     res = {"workload": f"the same volume, {n_iter} accelerated iterations (Biggs-Andrews)",
            "ms": round(ms, 3), "ms_per_iter": round(ms_it, 4), "plain_ms_per_iter": round(plain_ms_per_iter, 4),
            "value": round(int(d.numel()) * n_iter / (ms * 1e-3) / 1e9, 3), "unit": "Gvoxel-iter/s",
            "alpha_last": round(float(alpha[-1].item()), 4),
            "poisson_nll": {"accel": nll_acc, **{f"plain_{n}": v for n, v in curve.items()}},
-           "plain_iters_to_match": match if match is not None else f">{4 * n_iter}"}
+           "plain_iters_to_match": [lower, match] if match is not None else f">{16 * n_iter}",
+           "kernels": kern}
     if match is not None:
-        res["time_to_same_nll_speedup"] = round(match * plain_ms_per_iter / ms, 3)
+        # plain RL needs more than `lower` and at most `match` iterations for the same likelihood
+        res["time_to_same_nll_speedup"] = [round(lower * plain_ms_per_iter / ms, 3),
+                                           round(match * plain_ms_per_iter / ms, 3)]
     return res
 
 

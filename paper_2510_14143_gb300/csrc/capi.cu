@@ -1586,10 +1586,19 @@ __global__ void __launch_bounds__(1024) k_acc_alpha(const float4 *__restrict__ p
 {
     __shared__ CFloat sn[1024], sd[1024];
     CFloat num{0.f, 0.f}, den{0.f, 0.f};
-    for (int64_t i = threadIdx.x; i < nblocks; i += blockDim.x) {
-        const float4 q = part[i];
-        num = cf_merge(num, CFloat{q.x, q.y});
-        den = cf_merge(den, CFloat{q.z, q.w});
+    constexpr int U = 8;  // loads in flight per thread
+    for (int64_t i0 = threadIdx.x; i0 < nblocks; i0 += (int64_t)U * blockDim.x) {
+        float4 q[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x;
+            q[u] = i < nblocks ? part[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            num = cf_merge(num, CFloat{q[u].x, q[u].y});
+            den = cf_merge(den, CFloat{q[u].z, q[u].w});
+        }
     }
     sn[threadIdx.x] = num;
     sd[threadIdx.x] = den;

@@ -263,15 +263,19 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             const float al = *a.acc_alpha;
             const float *p0 = a.acc_prev + r0 * N, *p1 = a.acc_prev + r1 * N;
             float *y0 = a.acc_y + r0 * N, *y1 = a.acc_y + r1 * N;
+            // every load before the first store, so none waits behind a store it might alias
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
                 const float x0 = ok0 ? __ldg(s0 + n) : 0.f, x1 = ok1 ? __ldg(s1 + n) : 0.f;
                 const float q0 = ok0 ? __ldg(p0 + n) : 0.f, q1 = ok1 ? __ldg(p1 + n) : 0.f;
-                const float w0 = fmaxf(fmaf(al, x0 - q0, x0), 0.f), w1 = fmaxf(fmaf(al, x1 - q1, x1), 0.f);
-                if (ok0) y0[n] = w0;
-                if (ok1) y1[n] = w1;
-                v[i] = make_float2(w0, w1);
+                v[i] = make_float2(fmaxf(fmaf(al, x0 - q0, x0), 0.f), fmaxf(fmaf(al, x1 - q1, x1), 0.f));
+            });
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                const int n = t + P * i;
+                if (ok0) y0[n] = v[i].x;
+                if (ok1) y1[n] = v[i].y;
             });
         } else {
             static_for<0, E>([&](auto i_) {
@@ -356,6 +360,19 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             const bool acc = MODE == XM_FINAL && a.acc_g != nullptr;
             const bool acc_prev = a.acc_gprev != nullptr;
             CFloat c_num{0.f, 0.f}, c_den{0.f, 0.f};
+            // g_{k-1}, loaded ahead of the loop: its stores could alias it as far as the
+            // compiler knows, which would serialise each load behind the previous store
+            float gp0[MODE == XM_FINAL ? E : 1], gp1[MODE == XM_FINAL ? E : 1];
+            if constexpr (MODE == XM_FINAL) {
+                if (acc && acc_prev) {
+                    const float *h0 = a.acc_gprev + r0 * N, *h1 = a.acc_gprev + r1 * N;
+                    static_for<0, E>([&](auto i_) {
+                        constexpr int i = CUBIC_CI(i_);
+                        gp0[i] = ok0 ? __ldg(h0 + t + P * i) : 0.f;
+                        gp1[i] = ok1 ? __ldg(h1 + t + P * i) : 0.f;
+                    });
+                }
+            }
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
@@ -371,11 +388,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
                         const float g0 = x0 - u0v, g1 = x1 - u1v;  // 0 on rows past the end
                         if (ok0) a.acc_g[r0 * N + n] = g0;
                         if (ok1) a.acc_g[r1 * N + n] = g1;
-                        if (acc_prev) {
-                            const float h0 = ok0 ? __ldg(a.acc_gprev + r0 * N + n) : 0.f;
-                            const float h1 = ok1 ? __ldg(a.acc_gprev + r1 * N + n) : 0.f;
-                            c_num = cf_add(cf_add(c_num, g0 * h0), g1 * h1);
-                        }
+                        if (acc_prev) c_num = cf_add(cf_add(c_num, g0 * gp0[i]), g1 * gp1[i]);
                         c_den = cf_add(cf_add(c_den, g0 * g0), g1 * g1);
                     }
                 }
