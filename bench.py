@@ -276,6 +276,8 @@ def run_ours(args, w: synth.Workload):
     }
     if not args.no_accel:
         result["accel"] = run_accel(cr, args, plan, d, n_iter, eps, ms / args.steps / n_iter)
+    if not args.no_paper_shape:
+        result["paper_shape"] = run_paper_shape(cr, args)
     if not args.no_batched:
         result["batched"] = run_batched(cr, args)
     if not args.no_grad:
@@ -388,6 +390,53 @@ def run_accel(cr, args, plan, d, n_iter: int, eps: float, plain_ms_per_iter: flo
         res["time_to_same_nll_speedup"] = [round(lower * plain_ms_per_iter / ms, 3),
                                            round(match * plain_ms_per_iter / ms, 3)]
     return res
+
+
+def run_paper_shape(cr, args):
+    """The paper's stack shape, ZYX 30 x 2160 x 2560 with a PSF of the same size (circular FFT
+    convolution), 50 iterations: Gvoxel-iter/s and the top kernel's HBM fraction."""
+    import torch
+    w = synth.PAPER
+    shape, V, n_iter, eps = w.shape, w.voxels, w.n_iter, 1e-6
+    g = torch.Generator(device="cuda").manual_seed(w.seed)
+    lam = 20.0 + 300.0 * torch.rand(shape, device="cuda", generator=g) ** 12
+    d = torch.poisson(lam, generator=g)
+    del lam
+    psf = torch.empty(shape, dtype=torch.float32, device="cuda")
+    cr.cubic_psf_gaussian(shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0, psf)
+    plan = cr.cubic_rl_plan(shape, psf)
+    del psf
+    out = torch.empty_like(d)
+    cr.cubic_rl_autotune(plan, d, out)
+    stream = torch.cuda.current_stream()
+    cr.cubic_rl_deconvolve(plan, d, n_iter, eps, out)
+    reps = 2
+    cr.cubic_rl_profile(plan, True, max_events=2 * (n_iter * 8 + 8) * reps + 64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        cr.cubic_rl_deconvolve(plan, d, n_iter, eps, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    prof = cr.cubic_rl_profile_read(plan)
+    cr.cubic_rl_profile(plan, False)
+    kernels = {k: v for k, v in prof.items() if v["timed"] > 0}
+    total = sum(v["ms"] for v in kernels.values())
+    peak, _ = hbm_peak()
+    per = {k: {"share": round(v["ms"] / total, 4), "avg_us": round(v["ms"] / v["timed"] * 1e3, 2),
+               "frac": round(v["bytes"] / v["launches"] / (v["ms"] / v["timed"] * 1e-3) / 1e9 / peak, 4)}
+           for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["ms"])}
+    value = V * n_iter / (ms * 1e-3) / 1e9
+    return {"workload": f"{w.name}: ZYX {shape[0]}x{shape[1]}x{shape[2]}, same-size Gaussian PSF "
+                        f"(sigma {w.psf_sigma_xy}, {w.psf_sigma_z}), {n_iter} iterations, Poisson data generated "
+                        "on the device",
+            "value": round(value, 3), "unit": UNIT, "ms": round(ms, 3),
+            "model_84B_frac": round(value * 84.0 / peak, 4),
+            "variants_xyz": list(cr.cubic_rl_plan_variants(plan)[1]),
+            "flux_rel_err": abs(out.double().sum().item() / d.double().sum().item() - 1.0),
+            "kernels": per}
 
 
 def run_fwd_bwd(cr, args):
@@ -558,6 +607,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--no-grad", action="store_true", help="skip the forward+backward leg")
     ap.add_argument("--no-accel", action="store_true", help="skip the accelerated-RL leg")
+    ap.add_argument("--no-paper-shape", action="store_true", help="skip the 2560x2160x30 leg")
     ap.add_argument("--ncu-target", metavar="VX,VY,VZ",
                     help="profiling target only: plan + --ncu-iters RL iterations with these launch shapes")
     ap.add_argument("--ncu-iters", type=int, default=1)

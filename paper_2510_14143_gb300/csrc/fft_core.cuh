@@ -133,12 +133,13 @@ constexpr int plan_span(int N, int E, int stage)
 }
 
 // Stage twiddle tables: for stage s >= 1 (radix R, span Ns) the table holds
-// W_{Ns R}^{k r} at [r][k] (r < R, k < Ns), so lanes with consecutive k read
-// consecutive words.  Tables of all stages are stored back to back.
+// W_{Ns R}^{k r} at [r - 1][k] (1 <= r < R, k < Ns; the r = 0 row is all ones and is
+// not stored), so lanes with consecutive k read consecutive words.  Tables of all
+// stages are stored back to back.
 constexpr int tw_stage_offset(int N, int E, int stage)
 {
     int off = 0;
-    for (int s = 1; s < stage; ++s) off += plan_radix(N, E, s) * plan_span(N, E, s);
+    for (int s = 1; s < stage; ++s) off += (plan_radix(N, E, s) - 1) * plan_span(N, E, s);
     return off;
 }
 
@@ -354,8 +355,8 @@ struct LineFFT {
             constexpr int Ns = plan_span(N, E, s);
             constexpr int TS = N / (Ns * R);
             float2 *dst = smem_tw + tw_stage_offset(N, E, s);
-            for (int i = tid; i < R * Ns; i += nthreads) {
-                const int r = i / Ns, k = i % Ns;
+            for (int i = tid; i < (R - 1) * Ns; i += nthreads) {
+                const int r = 1 + i / Ns, k = i % Ns;
                 dst[i] = __ldg(tw_global + k * r * TS);
             }
         });
@@ -389,7 +390,7 @@ struct LineFFT {
                         const float2 *ts = tw + tw_stage_offset(N, E, s) + k;
                         static_for<1, R>([&](auto r_) {
                             constexpr int r = CUBIC_CI(r_);
-                            x[r] = cmul(x[r], ts[r * Ns]);
+                            x[r] = cmul(x[r], ts[(r - 1) * Ns]);
                         });
                     } else {
                         static_for<1, R>([&](auto r_) {

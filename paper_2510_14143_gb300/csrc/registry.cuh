@@ -235,6 +235,18 @@ cudaError_t launch_z_tma(const ZArgs &a, cudaStream_t st)
 }
 
 // Y and Z tile widths and stage counts may differ: the Z pass also stages H.
+// widest plain (non-TMA) Y/Z column tile, 16, 8 or 4 columns, whose CTA fits: B * N
+// complex elements plus the twiddle table in shared memory, and at most 512 threads
+// (more would cap the long lines' transforms below their register needs)
+template <int N, int P>
+constexpr int plain_cols()
+{
+    constexpr size_t tw = (size_t)tw_table_size(N, N / P) * sizeof(float2);
+    return (16 * N * sizeof(float2) + tw <= 220 * 1024 && P * 16 <= 512)  ? 16
+           : (8 * N * sizeof(float2) + tw <= 220 * 1024 && P * 8 <= 512) ? 8
+                                                                           : 4;
+}
+
 template <int N, int P, int BY, int NSY, int BZ, int NSZ>
 YZVariant make_yzvariant_tma()
 {
@@ -245,24 +257,36 @@ YZVariant make_yzvariant_tma()
     if constexpr (BY > 0)
         v.y = launch_y_tma<N, P, BY, NSY>;
     else
-        v.y = launch_y<N, P, 16>;
+        v.y = launch_y<N, P, plain_cols<N, P>()>;
     if constexpr (BZ > 0)
         v.z = launch_z_tma<N, P, BZ, NSZ>;
     else
-        v.z = launch_z<N, P, 16>;
+        v.z = launch_z<N, P, plain_cols<N, P>()>;
     return v;
 }
 
 constexpr size_t kTmaSmemBudget = 220 * 1024;
 
-// widest column tile (16 or 8) with at least two stages in the budget
+// A TMA tile of B columns fits when two stages fit the budget, the CTA has at most 1024
+// threads and every box of the tile starts on a 128-byte boundary in shared memory
+// (boxes of box_rows(N) rows sit at multiples of box_rows(N) * B * 8 bytes).
+template <int N, int P, int B, int KIND>
+constexpr bool tma_tile_fits()
+{
+    return col_smem_bytes<N, P, B, KIND, 2>() <= kTmaSmemBudget && P * B <= 1024 &&
+           (N <= 256 || (box_rows(N) * B) % 16 == 0);
+}
+
+// widest column tile that fits: 16 or 8 columns, or 4 for lines longer than 1024;
+// 0: no TMA variant
 template <int N, int KIND>
 constexpr int tma_cols()
 {
     constexpr int P = AxisShape<N>::P0;
-    return col_smem_bytes<N, P, 16, KIND, 2>() <= kTmaSmemBudget ? 16
-           : col_smem_bytes<N, P, 8, KIND, 2>() <= kTmaSmemBudget ? 8
-                                                                   : 0;
+    return tma_tile_fits<N, P, 16, KIND>()                ? 16
+           : tma_tile_fits<N, P, 8, KIND>()               ? 8
+           : (N > 1024 && tma_tile_fits<N, P, 4, KIND>()) ? 4
+                                                          : 0;
 }
 
 // most stages (2..4) that fit the budget at that width, for thread split P.
@@ -375,9 +399,10 @@ AxisKernels make_axis()
     k.xm[XM_UPDATE] = launch_x_multi<N, P0, XL, XM_UPDATE>;
     k.xm[XM_FINAL] = launch_x_multi<N, P0, XL, XM_FINAL>;
     k.xm_lines = XL;
-    k.ym = launch_y_multi<N, P0, 16>;
-    k.zm = launch_z_multi<N, P0, 16>;
-    k.m_cols = 16;
+    constexpr int B0 = plain_cols<N, P0>();
+    k.ym = launch_y_multi<N, P0, B0>;
+    k.zm = launch_z_multi<N, P0, B0>;
+    k.m_cols = B0;
     k.nyz = 0;
     constexpr int BY = tma_cols<N, COL_Y>(), BZ = tma_cols<N, COL_Z>();
     if constexpr (S::kTuned && (BY > 0 || BZ > 0)) {
@@ -399,13 +424,19 @@ AxisKernels make_axis()
                 push_yz(k, make_yzvariant_tma<N, P1, BY, NY1, 32, 2>());
         }
     }
-    push_yz(k, make_yzvariant<N, P0, 16>());
+    push_yz(k, make_yzvariant<N, P0, B0>());
+    if constexpr (!S::kTuned && N >= 8 && BY > 0 && P0 * 64 <= 1024 && tma_tile_fits<N, P0, 64, COL_Z>()) {
+        // short lines have one or two threads each: a TMA variant whose Z tile is 64
+        // columns wide gives the CTA enough threads (thin stacks, e.g. 30 slices)
+        push_yz(k, make_yzvariant_tma<N, P0, BY, 2, 64, 2>());
+    }
     if constexpr (S::kTuned) {
-        push_yz(k, make_yzvariant<N, P0, 8>());
+        if constexpr (B0 == 16) push_yz(k, make_yzvariant<N, P0, 8>());
         if constexpr (S::kAlt) {
             constexpr int P1 = S::P1;
             if constexpr (N < 256) push_x(k, make_xvariant<N, P1, S::lines(P1, 128)>());
-            push_yz(k, make_yzvariant<N, P1, 8>());
+            constexpr int B1 = plain_cols<N, P1>() < 8 ? plain_cols<N, P1>() : 8;
+            push_yz(k, make_yzvariant<N, P1, B1>());
         }
     }
     return k;
@@ -416,7 +447,7 @@ AxisKernels make_axis()
 constexpr int kLengths[] = {1,   2,   3,   4,   5,   6,   8,   9,   10,  12,  15,  16,  18,  20,  24,
                             25,  27,  30,  32,  36,  40,  45,  48,  50,  54,  60,  64,  72,  75,  80,
                             81,  90,  96,  100, 108, 120, 125, 128, 135, 144, 150, 160, 192, 256, 320,
-                            384, 512, 640, 768, 1024};
+                            384, 512, 640, 768, 1024, 2160, 2304, 2560, 2592};
 constexpr int kNumLengths = sizeof(kLengths) / sizeof(kLengths[0]);
 constexpr int kShards = 16;
 

@@ -58,12 +58,16 @@ class Workload:
         return int(np.prod(self.xyz))
 
 
-# Plain single-volume workloads (64x64x32, 256x256x128, 1024x1024x128).
+# Plain single-volume workloads (64x64x32, 256x256x128, 1024x1024x128, 2560x2160x30).
 SMALL = Workload("rl_64x64x32", (64, 64, 32), 12, (2.0, 4.0), 10.0, 1.5, 3.0, 20, SEED_BASE + 1)
 MEDIUM = Workload("rl_256x256x128", (256, 256, 128), 400, (2.0, 5.0), 10.0, 2.0, 5.0, 100, SEED_BASE + 2)
 LARGE = Workload("rl_1024x1024x128", (1024, 1024, 128), 20000, (2.0, 6.0), 20.0, 2.5, 6.0, 50,
                  SEED_BASE + 3)
-PLAIN = {w.name: w for w in (SMALL, MEDIUM, LARGE)}
+# The paper's stack shape (ZYX 30 x 2160 x 2560, a PSF of the same size), with the large
+# workload's blob density and PSF.
+PAPER = Workload("rl_2560x2160x30", (2560, 2160, 30), round(20000 * 2560 * 2160 * 30 / (1024 * 1024 * 128)),
+                 (2.0, 6.0), 20.0, 2.5, 6.0, 50, SEED_BASE + 5)
+PLAIN = {w.name: w for w in (SMALL, MEDIUM, LARGE, PAPER)}
 
 # Batched: 64 volumes, each axis drawn from SMOOTH_48_160, small-volume blob density.
 BATCH_COUNT = 64

@@ -48,7 +48,7 @@ def gpu_forward(cr, x):
 
 
 LEN = synth.SMOOTH_48_160 + (1, 2, 3, 4, 5, 6, 8, 9, 10, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32, 36, 40, 45,
-                             192, 256, 320, 384, 512, 640, 768, 1024)
+                             192, 256, 320, 384, 512, 640, 768, 1024, 2160, 2304, 2560, 2592)
 
 
 @pytest.mark.parametrize("axis", [0, 1, 2])
@@ -175,6 +175,20 @@ def test_rl_medium_workload_parity(cr):
     assert err <= 1e-4
 
 
+def test_rl_paper_shape_parity(cr):
+    # the paper's stack shape, ZYX 30 x 2160 x 2560 with a PSF of the same size, two
+    # iterations against the oracle over the whole volume
+    w = synth.PAPER
+    r = np.random.Generator(np.random.PCG64(w.seed))
+    d = r.poisson(20.0 + 300.0 * r.random(w.shape) ** 12).astype(np.float32)
+    psf = oracle.psf_gaussian(w.shape, w.psf_sigma_xy, w.psf_sigma_z).astype(np.float32)
+    got = run_rl(cr, d, psf, 2)
+    ref = oracle.rl(d, psf, 2, 1e-6)
+    err = rel_l2(got, ref)
+    print(f"rl 2560x2160x30, 2 it: rel-L2 = {err:.3e}")
+    assert err <= 1e-5
+
+
 def test_errors_are_reported(cr):
     shape = (4, 4, 4)
     psf = dev(np.ones(shape, np.float32) / 64)
@@ -198,7 +212,8 @@ def test_errors_are_reported(cr):
     assert e.value.status == 2
 
 
-@pytest.mark.parametrize("shape", [(64, 96, 128), (128, 80, 64), (16, 256, 100), (8, 1024, 1024)])
+@pytest.mark.parametrize("shape", [(64, 96, 128), (128, 80, 64), (16, 256, 100), (8, 1024, 1024),
+                                   (3, 2160, 2560), (6, 2592, 4), (2560, 3, 2304), (30, 45, 16), (60, 8, 32)])
 def test_every_launch_variant_matches_oracle(cr, shape):
     # each compiled launch shape of each pass computes the same convolution
     r = np.random.default_rng(sum(shape))
