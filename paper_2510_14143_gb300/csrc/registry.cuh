@@ -392,6 +392,10 @@ AxisKernels make_axis()
         k.xv[0] = make_xvariant<N, P0, S::lines(P0, 128)>();
         k.nx = 1;
     }
+    // lines longer than 1024: a split with up to 40 elements per thread may need fewer
+    // stages (2560: 40 x 8 x 8 instead of 20 x 4 x 4 x 4 x 2)
+    constexpr int PW = N > 1024 ? choose_threads(N, 40) : -1;
+    if constexpr (PW > 0 && PW != P0 && PW != S::P1) push_x(k, make_xvariant<N, PW, S::lines(PW, 128)>());
     constexpr int XL = S::lines(P0, 128);
     k.xm[XM_FWD] = launch_x_multi<N, P0, XL, XM_FWD>;
     k.xm[XM_INV] = launch_x_multi<N, P0, XL, XM_INV>;
