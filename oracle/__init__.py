@@ -72,6 +72,9 @@ def _load():
                 "orc_fsc": ([P, P, i64, i64, i64, ci, P, P, P, P], ci),
                 "orc_rl_auto": ([P, P, i64, i64, i64, ci, cd, cd, ci, P, ctypes.POINTER(ci), P], ci),
                 "orc_rl_accel": ([P, P, i64, i64, i64, ci, cd, P, P], ci),
+                "orc_poisson_nll": ([P, P, i64, cd], cd),
+                "orc_psnr_si": ([P, P, i64], cd),
+                "orc_rl_monitor": ([P, P, P, i64, i64, i64, ci, cd, ci, cd, ci, P, ctypes.POINTER(ci), P], ci),
                 "orc_accel_linear": ([i64, ci, P, P, P, P, P], ci),
                 "orc_psf_gaussian": ([i64, i64, i64, cd, cd, cd, P], ci),
                 "orc_psf_gaussian_grad": ([i64, i64, i64, cd, cd, cd, P, P], ci),
@@ -193,6 +196,34 @@ def rl_auto(d, psf, max_iter: int, eps: float, tol: float, check_every: int = 1)
     n = ctypes.c_int(0)
     _check(_load().orc_rl_auto(_p(dd), _p(p), *dd.shape, int(max_iter), float(eps), float(tol), int(check_every),
                                _p(out), ctypes.byref(n), _p(hist)), "rl_auto")
+    return out, int(n.value), hist[:n.value].copy()
+
+
+def poisson_nll(b, d, eps: float) -> float:
+    """sum(c - d ln c), c = max(b, eps)."""
+    bb, dd = _f64(b), _f64(d)
+    return float(_load().orc_poisson_nll(_p(bb), _p(dd), bb.size, float(eps)))
+
+
+def psnr_si(x, y) -> float:
+    """Scale-invariant PSNR of x against the reference y (best affine fit of x to y)."""
+    xx, yy = _f64(x), _f64(y)
+    return float(_load().orc_psnr_si(_p(xx), _p(yy), xx.size))
+
+
+METRIC_REL_CHANGE, METRIC_NLL, METRIC_PSNR = 0, 1, 2
+
+
+def rl_monitor(d, psf, max_iter: int, eps: float, metric: int, tol: float, check_every: int = 1, ref=None):
+    """RL with metric-guided stopping; returns (estimate, iterations done, history[n, 3])."""
+    dd, p = _f64(d), _f64(psf)
+    rr = None if ref is None else _f64(ref)
+    out = np.empty_like(dd)
+    hist = np.zeros((max(1, int(max_iter)), 3), np.float64)
+    n = ctypes.c_int(0)
+    _check(_load().orc_rl_monitor(_p(dd), _p(p), None if rr is None else _p(rr), *dd.shape, int(max_iter),
+                                  float(eps), int(metric), float(tol), int(check_every), _p(out), ctypes.byref(n),
+                                  _p(hist)), "rl_monitor")
     return out, int(n.value), hist[:n.value].copy()
 
 

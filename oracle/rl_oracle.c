@@ -415,6 +415,109 @@ int orc_rl_auto(const double *d, const double *psf, int64_t nz, int64_t ny, int6
     return rc;
 }
 
+/* Quality metrics for metric-guided stopping (the paper's Section 4 stops RL when the
+ * improvement of an image-quality measure between consecutive iterations falls under a
+ * threshold; Section 3 lists scale-invariant PSNR among its metrics).
+ *   Poisson negative log-likelihood (up to a constant): NLL(u) = sum (c - d ln c),
+ *     c = max(h * u, eps), the objective RL maximises the likelihood of.
+ *   Scale-invariant PSNR of x against a reference y (Weigert et al. 2018): the affine map
+ *     a x + b closest to y in least squares, then 20 log10(range(y) / rmse),
+ *     range(y) = max y - min y, rmse = sqrt(min_{a,b} mean((a x + b - y)^2)).  The
+ *     minimum has the closed form var(y) - cov(x, y)^2 / var(x) (population moments);
+ *     var(x) = 0 leaves var(y).  A zero rmse gives +inf, a zero range -inf. */
+double orc_poisson_nll(const double *b, const double *d, int64_t V, double eps)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < V; ++i) {
+        double c = b[i] > eps ? b[i] : eps;
+        s += c - d[i] * log(c);
+    }
+    return s;
+}
+
+double orc_psnr_si(const double *x, const double *y, int64_t V)
+{
+    double mx = 0.0, my = 0.0, ymin = y[0], ymax = y[0];
+    for (int64_t i = 0; i < V; ++i) {
+        mx += x[i];
+        my += y[i];
+        if (y[i] < ymin) ymin = y[i];
+        if (y[i] > ymax) ymax = y[i];
+    }
+    mx /= (double)V;
+    my /= (double)V;
+    double vx = 0.0, vy = 0.0, cxy = 0.0;
+    for (int64_t i = 0; i < V; ++i) {
+        double ex = x[i] - mx, ey = y[i] - my;
+        vx += ex * ex;
+        vy += ey * ey;
+        cxy += ex * ey;
+    }
+    vx /= (double)V;
+    vy /= (double)V;
+    cxy /= (double)V;
+    double mse = vx > 0.0 ? vy - cxy * cxy / vx : vy;
+    if (mse < 0.0) mse = 0.0;
+    return 20.0 * log10((ymax - ymin) / sqrt(mse));
+}
+
+/* RL with metric-guided stopping.  After iteration k (which made u_{k+1}) the history
+ * row k holds (delta_k, NLL(u_k), PSNR_si(u_{k+1}, ref)); NAN for the PSNR without a
+ * reference.  NLL(u_k) comes from iteration k's forward convolution.  At every check
+ * (k+1 a multiple of check_every, or k+1 = max_iter) the run stops when the chosen
+ * measure's improvement is under tol:
+ *   metric 0: delta_k < tol (relative change of the estimate);
+ *   metric 1: k >= 1 and (NLL(u_{k-1}) - NLL(u_k)) / |NLL(u_k)| < tol;
+ *   metric 2: k >= 1 and PSNR_k - PSNR_{k-1} < tol (decibels; needs ref).
+ * out: the last estimate u_{n_done}. */
+int orc_rl_monitor(const double *d, const double *psf, const double *ref, int64_t nz, int64_t ny, int64_t nx,
+                   int max_iter, double eps, int metric, double tol, int check_every, double *out, int *n_done,
+                   double *hist)
+{
+    if (!d || !psf || !out || !n_done || !hist || nz < 1 || ny < 1 || nx < 1 || max_iter < 1 ||
+        check_every < 1 || !(eps > 0) || metric < 0 || metric > 2 || (metric == 2 && !ref))
+        return -1;
+    int64_t V = nz * ny * nx;
+    double *Hs = malloc(sizeof(double) * 2 * (size_t)V);
+    double *u = malloc(sizeof(double) * (size_t)V);
+    double *un = malloc(sizeof(double) * (size_t)V);
+    double *b = malloc(sizeof(double) * (size_t)V);
+    if (!Hs || !u || !un || !b) { free(Hs); free(u); free(un); free(b); return -2; }
+    int rc = orc_psf_spectrum(psf, Hs, nz, ny, nx);
+    double u0 = orc_initial_value(d, V, eps);
+    for (int64_t i = 0; i < V; ++i) u[i] = u0;
+    int k = 0;
+    while (!rc && k < max_iter) {
+        rc = orc_rl_iterate(Hs, d, u, eps, nz, ny, nx, un, b, NULL, NULL);
+        if (rc) break;
+        double num = 0.0, den = 0.0;
+        for (int64_t i = 0; i < V; ++i) {
+            double e = un[i] - u[i];
+            num += e * e;
+            den += u[i] * u[i];
+        }
+        double *h = hist + 3 * (size_t)k;
+        h[0] = den > 0 ? sqrt(num / den) : 0.0;
+        h[1] = orc_poisson_nll(b, d, V, eps);
+        h[2] = ref ? orc_psnr_si(un, ref, V) : NAN;
+        memcpy(u, un, sizeof(double) * (size_t)V);
+        ++k;
+        if (k % check_every == 0 || k == max_iter) {
+            int stop = 0;
+            if (metric == 0) stop = h[0] < tol;
+            else if (k >= 2 && metric == 1) stop = (h[-2] - h[1]) / fabs(h[1]) < tol;
+            else if (k >= 2 && metric == 2) stop = h[2] - h[-1] < tol;
+            if (stop) break;
+        }
+    }
+    if (!rc) {
+        memcpy(out, u, sizeof(double) * (size_t)V);
+        *n_done = k;
+    }
+    free(Hs); free(u); free(un); free(b);
+    return rc;
+}
+
 /* Accelerated Richardson-Lucy.  The paper (Section 2, on the pycudadecon plugin) cites
  * the acceleration of Biggs and Andrews ("Acceleration of iterative image restoration
  * algorithms", Applied Optics 36(8), 1997).  Their first-order vector extrapolation

@@ -620,3 +620,68 @@ def test_rl_accel_flux_nonnegativity_and_speedup():
         return float(np.sum(b - d * np.log(np.maximum(b, 1e-6))))
 
     assert nll(x) < nll(oracle.rl(d, psf, 2 * n, 1e-6))
+
+
+# ---------------------------------------------- metric-guided stopping: NLL, PSNR
+
+def test_poisson_nll_closed_form_and_clamp():
+    r = np.random.default_rng(81)
+    d = r.uniform(1, 50, 200)
+    assert np.isclose(oracle.poisson_nll(d, d, 1e-6), np.sum(d - d * np.log(d)), rtol=1e-14)
+    b = d.copy()
+    b[:10] = -3.0       # clamped to eps
+    expect = np.sum(d[10:] - d[10:] * np.log(d[10:])) + np.sum(0.5 - d[:10] * np.log(0.5))
+    assert np.isclose(oracle.poisson_nll(b, d, 0.5), expect, rtol=1e-14)
+
+
+def test_psnr_si_closed_form_and_invariance():
+    r = np.random.default_rng(82)
+    y = r.uniform(0, 10, 1000)
+    e = r.standard_normal(1000)
+    A = np.stack([np.ones_like(y), y], 1)
+    e -= A @ np.linalg.lstsq(A, e, rcond=None)[0]      # e orthogonal to 1 and y
+    x = y + e
+    vy, ve = y.var(), e.var()
+    expect = 20 * np.log10((y.max() - y.min()) / np.sqrt(vy * ve / (vy + ve)))
+    assert np.isclose(oracle.psnr_si(x, y), expect, rtol=1e-12)
+    # invariant under any affine map of the estimate, a sign flip included
+    assert np.isclose(oracle.psnr_si(-2.5 * x + 7.0, y), expect, rtol=1e-12)
+    assert oracle.psnr_si(3.0 * y + 2.0, y) > 250     # exact up to rounding
+    assert oracle.psnr_si(np.full(1000, 4.0), y) == pytest.approx(20 * np.log10((y.max() - y.min()) / y.std()))
+
+
+def test_rl_monitor_history_recomputed():
+    d, xt = synth.workload_volume(synth.SMALL)
+    d = d.astype(np.float64)
+    psf = oracle.psf_gaussian(d.shape, 1.5, 3.0)
+    H = oracle.psf_spectrum(psf)
+    _, n, h = oracle.rl_monitor(d, psf, 6, 1e-6, oracle.METRIC_REL_CHANGE, 0.0, 1, xt)
+    assert n == 6
+    _, _, deltas = oracle.rl_auto(d, psf, 6, 1e-6, 0.0, 1)
+    assert np.allclose(h[:, 0], deltas, rtol=1e-12)
+    for k in range(6):
+        uk = oracle.rl(d, psf, k, 1e-6)
+        assert np.isclose(h[k, 1], oracle.poisson_nll(oracle.convolve(H, uk), d, 1e-6), rtol=1e-12)
+        assert np.isclose(h[k, 2], oracle.psnr_si(oracle.rl(d, psf, k + 1, 1e-6), xt), rtol=1e-12)
+    assert np.all(np.diff(h[:, 1]) <= 1e-9 * np.abs(h[1:, 1]))   # EM: the likelihood never falls
+    _, _, h2 = oracle.rl_monitor(d, psf, 3, 1e-6, oracle.METRIC_REL_CHANGE, 0.0, 1, None)
+    assert np.all(np.isnan(h2[:, 2]))
+
+
+def test_rl_monitor_stopping_rules():
+    d, xt = synth.workload_volume(synth.SMALL)
+    psf = oracle.psf_gaussian(d.shape, 1.5, 3.0)
+    _, _, h = oracle.rl_monitor(d, psf, 40, 1e-6, oracle.METRIC_REL_CHANGE, 0.0, 1, xt)
+    # PSNR: tol 0 stops after the first iteration whose PSNR is below the previous one
+    drop = next(k for k in range(1, 40) if h[k, 2] - h[k - 1, 2] < 0)
+    _, n, _ = oracle.rl_monitor(d, psf, 40, 1e-6, oracle.METRIC_PSNR, 0.0, 1, xt)
+    assert n == drop + 1
+    # NLL: the first check whose relative decrease is under tol
+    rel = (h[:-1, 1] - h[1:, 1]) / np.abs(h[1:, 1])
+    tol = 0.5 * (rel[10] + rel[11])
+    first = next(k for k in range(1, 40) if rel[k - 1] < tol)
+    _, n, _ = oracle.rl_monitor(d, psf, 40, 1e-6, oracle.METRIC_NLL, tol, 1, xt)
+    assert n == first + 1
+    # checks only every third iteration
+    _, n, _ = oracle.rl_monitor(d, psf, 40, 1e-6, oracle.METRIC_NLL, tol, 3, xt)
+    assert n % 3 == 0 and n >= first + 1 and n - 3 < first + 1
