@@ -183,6 +183,32 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve_noalloc(const int64_t dims[3], cons
                                                      const float *image, int n_iter, float eps,
                                                      float *out, void *stream);
 
+/* Richardson-Lucy with metric-guided stopping.  The paper (Section 4) selects the
+ * iteration count by monitoring an image-quality measure between consecutive iterations
+ * against a threshold; Section 3 lists scale-invariant PSNR among its metrics.  Every
+ * iteration k (the one that makes u_{k+1}) records three measures:
+ *   delta_k   = ||u_{k+1} - u_k|| / ||u_k||;
+ *   NLL(u_k)  = sum (c - d ln c), c = max(h * u_k, eps): the Poisson negative
+ *               log-likelihood up to a constant, from iteration k's forward convolution;
+ *   PSNR_k    = scale-invariant PSNR of u_{k+1} against reference: 20 log10(range / rmse)
+ *               after the least-squares affine fit a u + b of the estimate to the reference,
+ *               range = max - min of the reference (NaN without a reference).
+ * The sums are compensated float32 on the GPU; the fit and the logarithms are finished on
+ * the host in double precision.  At every check (k + 1 a multiple of check_every, or the
+ * last iteration) the run stops when the chosen measure's improvement is under tol:
+ *   CUBIC_METRIC_REL_CHANGE: delta_k < tol;
+ *   CUBIC_METRIC_NLL:        k >= 1 and (NLL(u_{k-1}) - NLL(u_k)) / |NLL(u_k)| < tol;
+ *   CUBIC_METRIC_PSNR:       k >= 1 and PSNR_k - PSNR_{k-1} < tol (decibels).
+ * out receives the last estimate, *n_done the iterations done, history (host, may be NULL)
+ * 3 * max_iter doubles: (delta, NLL, PSNR) per iteration done.  reference: device float32
+ * [nz][ny][nx] or NULL (required for CUBIC_METRIC_PSNR).  Synchronous: it returns after the
+ * last check.  Errors: INVALID_ARG, ALIGNMENT, OUT_OF_MEMORY, CUDA. */
+enum { CUBIC_METRIC_REL_CHANGE = 0, CUBIC_METRIC_NLL = 1, CUBIC_METRIC_PSNR = 2 };
+CUBIC_API cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, const float *image,
+                                                     const float *reference, int max_iter, float eps,
+                                                     int metric, double tol, int check_every, float *out,
+                                                     int *n_done, double *history, void *stream);
+
 /* Accelerated Richardson-Lucy.  The paper (Section 2) cites the acceleration of Biggs and
  * Andrews (Applied Optics 36(8), 1997) for RL; this is their first-order vector
  * extrapolation.  Each RL step starts from a prediction along the last move:

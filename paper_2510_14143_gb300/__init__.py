@@ -66,6 +66,8 @@ _SIGS = {
     "cubic_rl_deconvolve_auto": ([_vp, _vp, _ci, _cf, _cf, _ci, _vp, ctypes.POINTER(_ci),
                                   ctypes.POINTER(ctypes.c_double), _vp], _ci),
     "cubic_rl_deconvolve_accel": ([_vp, _vp, _ci, _cf, _vp, _vp, _vp], _ci),
+    "cubic_rl_deconvolve_monitor": ([_vp, _vp, _vp, _ci, _cf, _ci, ctypes.c_double, _ci, _vp, ctypes.POINTER(_ci),
+                                     ctypes.POINTER(ctypes.c_double), _vp], _ci),
     "cubic_rl_deconvolve_ckpt": ([_vp, _vp, _ci, _cf, _ci, _vp, _vp, _vp], _ci),
     "cubic_rl_backward_workspace_bytes": ([_vp, _ci, ctypes.POINTER(_sz)], _ci),
     "cubic_rl_backward": ([_vp, _vp, _ci, _cf, _ci, _vp, _vp, _vp, _vp, _ci, _vp], _ci),
@@ -305,6 +307,24 @@ def cubic_rl_deconvolve_auto(plan: Plan, image, max_iter: int, eps: float, tol: 
                                           _ptr(out, torch.float32, plan.voxels, "out"), ctypes.byref(n), hist,
                                           _stream(stream)), "cubic_rl_deconvolve_auto")
     return int(n.value), list(hist[:n.value])
+
+
+METRIC_REL_CHANGE, METRIC_NLL, METRIC_PSNR = 0, 1, 2
+
+
+def cubic_rl_deconvolve_monitor(plan: Plan, image, max_iter: int, eps: float, metric: int, tol: float,
+                                check_every: int, out, reference=None, stream=None):
+    """Metric-guided stopping; returns (iterations done, history as a list of (delta, NLL, PSNR))."""
+    import torch
+    n = _ci(0)
+    hist = (ctypes.c_double * (3 * max(1, int(max_iter))))()
+    ref = None if reference is None else _ptr(reference, torch.float32, plan.voxels, "reference")
+    _check(lib().cubic_rl_deconvolve_monitor(plan.handle, _ptr(image, torch.float32, plan.voxels, "image"), ref,
+                                             int(max_iter), float(eps), int(metric), float(tol), int(check_every),
+                                             _ptr(out, torch.float32, plan.voxels, "out"), ctypes.byref(n), hist,
+                                             _stream(stream)), "cubic_rl_deconvolve_monitor")
+    k = int(n.value)
+    return k, [tuple(hist[3 * i:3 * i + 3]) for i in range(k)]
 
 
 def cubic_rl_deconvolve_accel(plan: Plan, image, n_iter: int, eps: float, out, alpha=None, stream=None) -> None:

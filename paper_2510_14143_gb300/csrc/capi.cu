@@ -227,6 +227,9 @@ struct cubic_rl_plan_s {
     float *acc = nullptr;
     float4 *acc_part = nullptr;
     float *acc_state = nullptr;
+    // metric-guided stopping: per-iteration slots and records, owned
+    float *mon = nullptr;
+    int mon_cap = 0;
     bool allow_real_h = false;  // set by cubic_rl_plan (may allocate Hr)
     bool use_real_h = false;
     float *Hr = nullptr;        // [nz][ny][xp], owned
@@ -594,6 +597,7 @@ extern "C" cubic_status_t cubic_rl_plan_destroy(cubic_rl_plan_t plan)
     cudaFree(plan->auto_stats);
     cudaFree(plan->auto_delta);
     cudaFree(plan->acc);
+    cudaFree(plan->mon);
     for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
     delete plan;
     return CUBIC_OK;
@@ -1704,6 +1708,237 @@ extern "C" cubic_status_t cubic_rl_deconvolve_accel(cubic_rl_plan_t plan, const 
         std::swap(xc, xn);
         std::swap(gc, gn);
     }
+    return CUBIC_OK;
+}
+
+// ------------------------------------------------------------------ metric-guided stopping
+//
+// Three measures per iteration k (the one that made u_{k+1}), each in compensated float32
+// sums on the GPU:
+//   delta_k = ||u_{k+1} - u_k|| / ||u_k||          (update pass, as in automatic stopping)
+//   NLL(u_k) = sum (c - d ln c), c = max(h * u_k, eps)   (ratio pass)
+//   PSNR_si(u_{k+1}, y) against a reference y: sums of x, x^2, x y (k_ref_sums) and the
+//     reference's sum, sum of squares and range (k_ref_moments, once); the least-squares
+//     affine fit and the logarithm are finished on the host in double precision.
+// At each check the host applies the stopping rule of the chosen measure.
+
+constexpr int kMonBlocks = 608;  // reduction blocks: four per SM
+constexpr int kMonRec = 12;      // floats per iteration record
+
+// merges a CTA's compensated sums (NS of them, in order) into thread 0's registers
+template <int NS>
+__device__ __forceinline__ void block_merge_n(CFloat (&v)[NS])
+{
+    __shared__ CFloat red[NS][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = 0; j < NS; ++j)
+        for (int o = 16; o > 0; o >>= 1)
+            v[j] = cf_merge(v[j], CFloat{__shfl_down_sync(0xffffffffu, v[j].s, o),
+                                         __shfl_down_sync(0xffffffffu, v[j].c, o)});
+    if (lane == 0)
+        for (int j = 0; j < NS; ++j) red[j][warp] = v[j];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int j = 0; j < NS; ++j) {
+            v[j] = red[j][0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v[j] = cf_merge(v[j], red[j][w]);
+        }
+}
+
+// per-block (sum x, sum x^2, sum x y) as three (s, c) pairs
+__global__ void __launch_bounds__(256) k_ref_sums(const float *__restrict__ x, const float *__restrict__ y, int64_t V,
+                                                  float *__restrict__ part)
+{
+    CFloat v[3] = {};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        const float xv = x[i], yv = y[i];
+        v[0] = cf_add(v[0], xv);
+        v[1] = cf_add(v[1], xv * xv);
+        v[2] = cf_add(v[2], xv * yv);
+    }
+    block_merge_n<3>(v);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 3; ++j) {
+            part[6 * blockIdx.x + 2 * j] = v[j].s;
+            part[6 * blockIdx.x + 2 * j + 1] = v[j].c;
+        }
+}
+
+// per-block (sum y, sum y^2) as (s, c) pairs, then min y and max y
+__global__ void __launch_bounds__(256) k_ref_moments(const float *__restrict__ y, int64_t V, float *__restrict__ part)
+{
+    CFloat v[2] = {};
+    float mn = INFINITY, mx = -INFINITY;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        const float yv = y[i];
+        v[0] = cf_add(v[0], yv);
+        v[1] = cf_add(v[1], yv * yv);
+        mn = fminf(mn, yv);
+        mx = fmaxf(mx, yv);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    __shared__ float smn[32], smx[32];
+    if ((threadIdx.x & 31) == 0) {
+        smn[threadIdx.x >> 5] = mn;
+        smx[threadIdx.x >> 5] = mx;
+    }
+    block_merge_n<2>(v);  // synchronises: smn / smx are complete after it
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            mn = fminf(mn, smn[w]);
+            mx = fmaxf(mx, smx[w]);
+        }
+        part[6 * blockIdx.x + 0] = v[0].s;
+        part[6 * blockIdx.x + 1] = v[0].c;
+        part[6 * blockIdx.x + 2] = v[1].s;
+        part[6 * blockIdx.x + 3] = v[1].c;
+        part[6 * blockIdx.x + 4] = mn;
+        part[6 * blockIdx.x + 5] = mx;
+    }
+}
+
+// One iteration's record, merged in a fixed order: rec = (delta, nll s, nll c,
+// sx s, sx c, sxx s, sxx c, sxy s, sxy c) (value = s - c); ref_part may be null.
+__global__ void k_metrics(const float *__restrict__ dslots, const float *__restrict__ nslots,
+                          const float *__restrict__ ref_part, int nblk, float *__restrict__ rec)
+{
+    if (threadIdx.x != 0) return;
+    CFloat num{0.f, 0.f}, den{0.f, 0.f}, nll{0.f, 0.f};
+    for (int i = 0; i < 64; ++i) {
+        num = cf_merge(num, CFloat{dslots[4 * i], -dslots[4 * i + 1]});
+        den = cf_merge(den, CFloat{dslots[4 * i + 2], -dslots[4 * i + 3]});
+        nll = cf_merge(nll, CFloat{nslots[2 * i], -nslots[2 * i + 1]});
+    }
+    const float n = num.s - num.c, d = den.s - den.c;
+    rec[0] = d > 0.f ? sqrtf(n / d) : 0.f;
+    rec[1] = nll.s;
+    rec[2] = nll.c;
+    CFloat r[3] = {};
+    if (ref_part)
+        for (int b = 0; b < nblk; ++b)
+            for (int j = 0; j < 3; ++j) r[j] = cf_merge(r[j], CFloat{ref_part[6 * b + 2 * j], ref_part[6 * b + 2 * j + 1]});
+    for (int j = 0; j < 3; ++j) {
+        rec[3 + 2 * j] = r[j].s;
+        rec[4 + 2 * j] = r[j].c;
+    }
+}
+
+extern "C" cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, const float *image, const float *reference,
+                                                      int max_iter, float eps, int metric, double tol, int check_every,
+                                                      float *out, int *n_done, double *history, void *stream)
+{
+    if (!plan || !image || !out || !n_done) return fail(CUBIC_ERR_INVALID_ARG, "plan, image, out, n_done must be non-null");
+    if (max_iter < 1 || check_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "max_iter and check_every must be >= 1");
+    if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
+    if (!(tol >= -INFINITY) || tol != tol) return fail(CUBIC_ERR_INVALID_ARG, "tol must not be NaN");
+    if (metric < CUBIC_METRIC_REL_CHANGE || metric > CUBIC_METRIC_PSNR)
+        return fail(CUBIC_ERR_INVALID_ARG, "unknown metric %d", metric);
+    if (metric == CUBIC_METRIC_PSNR && !reference) return fail(CUBIC_ERR_INVALID_ARG, "the PSNR measure needs a reference");
+    if (!aligned16(image) || !aligned16(out) || (reference && !aligned16(reference)))
+        return fail(CUBIC_ERR_ALIGNMENT, "image, out and reference must be 16-byte aligned");
+    const size_t vb = (size_t)plan->V * sizeof(float);
+    if (overlaps(image, out, vb) || (reference && overlaps(reference, out, vb)))
+        return fail(CUBIC_ERR_INVALID_ARG, "out must not overlap image or reference");
+    cubic_rl_plan_s *p = plan;
+    cubic_status_t s = ensure_workspace(p);
+    if (s != CUBIC_OK) return s;
+    // [dslots: max_iter x 256][nslots: max_iter x 128][ref part: blocks x 6][ref moments: blocks x 6][rec: max_iter x 12]
+    const size_t f_d = (size_t)max_iter * 256, f_n = (size_t)max_iter * 128, f_r = (size_t)kMonBlocks * 6;
+    const size_t f_rec = (size_t)max_iter * kMonRec, total = f_d + f_n + 2 * f_r + f_rec;
+    if (p->mon_cap < max_iter) {
+        cudaDeviceSynchronize();
+        cudaFree(p->mon);
+        p->mon = nullptr;
+        p->mon_cap = 0;
+        void *m = nullptr;
+        CUBIC_CUDA(cudaMalloc(&m, total * sizeof(float)));
+        p->mon = (float *)m;
+        p->mon_cap = max_iter;
+    }
+    float *dslots = p->mon, *nslots = dslots + f_d, *rpart = nslots + f_n, *mpart = rpart + f_r, *rec = mpart + f_r;
+    cudaStream_t st = (cudaStream_t)stream;
+    CUBIC_CUDA(cudaMemsetAsync(p->mon, 0, (f_d + f_n) * sizeof(float), st));
+
+    // the reference's moments, once: sum y, sum y^2 (double on the host), range
+    double sy = 0.0, syy = 0.0, range = 0.0;
+    if (reference) {
+        k_ref_moments<<<kMonBlocks, 256, 0, st>>>(reference, p->V, mpart);
+        CUBIC_CUDA(cudaGetLastError());
+        std::vector<float> h((size_t)kMonBlocks * 6);
+        CUBIC_CUDA(cudaMemcpyAsync(h.data(), mpart, h.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+        CUBIC_CUDA(cudaStreamSynchronize(st));
+        float mn = INFINITY, mx = -INFINITY;
+        for (int b = 0; b < kMonBlocks; ++b) {
+            sy += (double)h[6 * b] - (double)h[6 * b + 1];
+            syy += (double)h[6 * b + 2] - (double)h[6 * b + 3];
+            mn = std::min(mn, h[6 * b + 4]);
+            mx = std::max(mx, h[6 * b + 5]);
+        }
+        range = (double)mx - (double)mn;
+    }
+    const double nV = (double)p->V;
+    auto psnr = [&](const float *r) -> double {
+        const double sx = (double)r[3] - (double)r[4], sxx = (double)r[5] - (double)r[6];
+        const double sxy = (double)r[7] - (double)r[8];
+        const double vx = sxx / nV - (sx / nV) * (sx / nV), vy = syy / nV - (sy / nV) * (sy / nV);
+        const double cxy = sxy / nV - (sx / nV) * (sy / nV);
+        double mse = vx > 0.0 ? vy - cxy * cxy / vx : vy;
+        if (mse < 0.0) mse = 0.0;
+        return 20.0 * log10(range / sqrt(mse));
+    };
+
+    if ((s = enqueue_init(p, image, eps, out, st)) != CUBIC_OK) return s;
+    XArgs xa = x_args(p);
+    xa.spec_in = p->ws;
+    xa.spec_out = p->ws;
+    xa.src = out;
+    xa.u = out;
+    xa.dst = out;
+    xa.d = image;
+    xa.eps = eps;
+    CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
+    std::vector<float> hrec;
+    std::vector<double> hist;  // [k][3]
+    int k = 0;
+    while (k < max_iter) {
+        if ((s = enqueue_yzy(p, p->ws, ZM_CONV, st)) != CUBIC_OK) return s;
+        XArgs xr = xa;
+        xr.nll_stats = nslots + (size_t)k * 128;
+        CUBIC_CUDA(run_x(p, XM_RATIO, xr, st));
+        if ((s = enqueue_yzy(p, p->ws, ZM_CORR, st)) != CUBIC_OK) return s;
+        XArgs xu = xa;
+        xu.stats = dslots + (size_t)k * 256;
+        CUBIC_CUDA(run_x(p, k + 1 < max_iter ? XM_UPDATE : XM_FINAL, xu, st));
+        if (reference) k_ref_sums<<<kMonBlocks, 256, 0, st>>>(out, reference, p->V, rpart);
+        k_metrics<<<1, 32, 0, st>>>(dslots + (size_t)k * 256, nslots + (size_t)k * 128, reference ? rpart : nullptr,
+                                    kMonBlocks, rec + (size_t)k * kMonRec);
+        CUBIC_CUDA(cudaGetLastError());
+        ++k;
+        if (k % check_every == 0 || k == max_iter) {
+            const int from = (int)hist.size() / 3;
+            hrec.resize((size_t)k * kMonRec);
+            CUBIC_CUDA(cudaMemcpyAsync(hrec.data() + (size_t)from * kMonRec, rec + (size_t)from * kMonRec,
+                                       (size_t)(k - from) * kMonRec * sizeof(float), cudaMemcpyDeviceToHost, st));
+            CUBIC_CUDA(cudaStreamSynchronize(st));
+            for (int j = from; j < k; ++j) {
+                const float *r = hrec.data() + (size_t)j * kMonRec;
+                hist.push_back((double)r[0]);
+                hist.push_back((double)r[1] - (double)r[2]);
+                hist.push_back(reference ? psnr(r) : NAN);
+            }
+            const double *h = hist.data() + 3 * (size_t)(k - 1);
+            bool stop = false;
+            if (metric == CUBIC_METRIC_REL_CHANGE) stop = h[0] < tol;
+            else if (k >= 2 && metric == CUBIC_METRIC_NLL) stop = (h[-2] - h[1]) / fabs(h[1]) < tol;
+            else if (k >= 2 && metric == CUBIC_METRIC_PSNR) stop = h[2] - h[-1] < tol;
+            if (stop) break;  // out holds u_k (the update wrote it)
+        }
+    }
+    *n_done = k;
+    if (history) std::copy(hist.begin(), hist.begin() + 3 * (size_t)k, history);
     return CUBIC_OK;
 }
 

@@ -68,6 +68,10 @@ struct XArgs {
     float *acc_g;
     const float *acc_gprev;
     float4 *acc_part;
+    // optional (XM_RATIO): adds the Poisson negative log-likelihood sum(c - d ln c),
+    // c = max(b, eps), into the compensated pair nll_stats[2 s], nll_stats[2 s + 1]
+    // (value = hi + lo), s = one of 64 slots
+    float *nll_stats;
 };
 
 struct YArgs {
@@ -194,6 +198,22 @@ __device__ __forceinline__ float4 block_merge2(CFloat a, CFloat b)
         b = red[1][0];
     }
     return make_float4(a.s, a.c, b.s, b.c);
+}
+
+// Adds each thread's compensated sum v into the pair (hi, lo) at pair[0], pair[1] of
+// a slot: a shuffle reduction where the warp is full (T threads in the CTA), else one
+// add per thread.
+template <int T>
+__device__ __forceinline__ void slot_add(float *pair, CFloat v)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((warp + 1) * 32 <= T) {
+        for (int o = 16; o > 0; o >>= 1)
+            v = cf_merge(v, CFloat{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)});
+        if (lane != 0) return;
+    }
+    catomic_add(pair, pair + 1, v.s);
+    catomic_add(pair, pair + 1, -v.c);
 }
 
 template <int N, int P, int L, int MODE>
@@ -335,6 +355,8 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             float *kb0 = a.keep_a + r0 * N, *kb1 = a.keep_a + r1 * N;
             float *kr0 = a.keep_b + r0 * N, *kr1 = a.keep_b + r1 * N;
             const bool keep = a.keep_a != nullptr;
+            const bool nll = a.nll_stats != nullptr;
+            CFloat c_nll{0.f, 0.f};
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
@@ -346,8 +368,17 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
                     if (ok0) { kb0[n] = v[i].x; kr0[n] = x0; }
                     if (ok1) { kb1[n] = v[i].y; kr1[n] = x1; }
                 }
+                if (nll) {
+                    const float c0 = fmaxf(v[i].x, eps), c1 = fmaxf(v[i].y, eps);
+                    if (ok0) c_nll = cf_add(c_nll, c0 - p0[n] * logf(c0));
+                    if (ok1) c_nll = cf_add(c_nll, c1 - p1[n] * logf(c1));
+                }
                 v[i] = make_float2(x0, x1);
             });
+            if (nll) {
+                const int slot = (int)((block * ((P * L + 31) / 32) + (threadIdx.x >> 5)) & 63);
+                slot_add<P * L>(a.nll_stats + 2 * slot, c_nll);
+            }
         } else if constexpr (MODE == XM_UPDATE || MODE == XM_FINAL) {
             // the update writes to dst when given (out of place), else over u
             float *ob = (MODE == XM_FINAL || a.dst) ? a.dst : a.u;
