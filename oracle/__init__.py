@@ -73,6 +73,8 @@ def _load():
                 "orc_rl_auto": ([P, P, i64, i64, i64, ci, cd, cd, ci, P, ctypes.POINTER(ci), P], ci),
                 "orc_rl_accel": ([P, P, i64, i64, i64, ci, cd, P, P], ci),
                 "orc_poisson_nll": ([P, P, i64, cd], cd),
+                "orc_conv_same": ([P, P, P, i64, i64, i64, i64, i64, i64, ci], ci),
+                "orc_rl_same": ([P, P, i64, i64, i64, i64, i64, i64, ci, cd, P], ci),
                 "orc_psnr_si": ([P, P, i64], cd),
                 "orc_rl_monitor": ([P, P, P, i64, i64, i64, ci, cd, ci, cd, ci, P, ctypes.POINTER(ci), P], ci),
                 "orc_accel_linear": ([i64, ci, P, P, P, P, P], ci),
@@ -197,6 +199,23 @@ def rl_auto(d, psf, max_iter: int, eps: float, tol: float, check_every: int = 1)
     _check(_load().orc_rl_auto(_p(dd), _p(p), *dd.shape, int(max_iter), float(eps), float(tol), int(check_every),
                                _p(out), ctypes.byref(n), _p(hist)), "rl_auto")
     return out, int(n.value), hist[:n.value].copy()
+
+
+def conv_same(psf, u, flipped: bool = False) -> np.ndarray:
+    """Linear ("same"-mode) convolution of u with a PSF of any box size (peak at floor(k/2));
+    flipped=True gives its adjoint."""
+    p, v = _f64(psf), _f64(u)
+    out = np.empty_like(v)
+    _check(_load().orc_conv_same(_p(p), _p(v), _p(out), *v.shape, *p.shape, int(flipped)), "conv_same")
+    return out
+
+
+def rl_same(d, psf, n_iter: int, eps: float = 1e-6) -> np.ndarray:
+    """RL with linear boundaries: the PSF box may be smaller than the image."""
+    dd, p = _f64(d), _f64(psf)
+    out = np.empty_like(dd)
+    _check(_load().orc_rl_same(_p(dd), _p(p), *dd.shape, *p.shape, int(n_iter), float(eps), _p(out)), "rl_same")
+    return out
 
 
 def poisson_nll(b, d, eps: float) -> float:

@@ -415,6 +415,115 @@ int orc_rl_auto(const double *d, const double *psf, int64_t nz, int64_t ny, int6
     return rc;
 }
 
+/* Linear ("same"-mode) boundaries: the image lives on its own box only, the PSF (dims
+ * kz, ky, kx, peak at floor(k/2)) can be smaller, and the convolution sees zeros outside the
+ * box instead of wrapping around:
+ *   b(x) = sum_t p(t + c) u(x - t),  c = floor(k/2), u = 0 outside [0, n)   ("same" output),
+ *   q(x) = sum_t p(t + c) r(x + t),  r = 0 outside [0, n)                    (its adjoint).
+ * Computed by FFT on the padded box M = n + k - 1 per axis, where circular convolution of
+ * the zero-padded arrays equals the linear one; the PSF is placed with its peak at the
+ * origin of the padded box.  The RL iteration is unchanged otherwise (x_0 = max(mean(d),
+ * eps) on the image box, r = d / max(b, eps)).  This is the zero-padded reading of the
+ * survey's "next" row; the paper's own workload uses a PSF of the image's size. */
+static void same_embed_psf(const double *psf, int64_t kz, int64_t ky, int64_t kx, double *h0, int64_t mz,
+                           int64_t my, int64_t mx)
+{
+    memset(h0, 0, sizeof(double) * (size_t)(mz * my * mx));
+    for (int64_t z = 0; z < kz; ++z)
+        for (int64_t y = 0; y < ky; ++y)
+            for (int64_t x = 0; x < kx; ++x)
+                h0[(wrap(z - kz / 2, mz) * my + wrap(y - ky / 2, my)) * mx + wrap(x - kx / 2, mx)] =
+                    psf[(z * ky + y) * kx + x];
+}
+
+struct same_geom {
+    int64_t nz, ny, nx, mz, my, mx;
+};
+
+/* out (image box) = crop(Re IDFT3(M(H) DFT3(pad(in)))), M = identity or conj */
+static int same_filter(const struct same_geom *g, const cplx *H, const double *in, double *out, cplx *work,
+                       int conjugate)
+{
+    int64_t Vm = g->mz * g->my * g->mx;
+    for (int64_t i = 0; i < Vm; ++i) work[i] = 0.0;
+    for (int64_t z = 0; z < g->nz; ++z)
+        for (int64_t y = 0; y < g->ny; ++y)
+            for (int64_t x = 0; x < g->nx; ++x)
+                work[(z * g->my + y) * g->mx + x] = in[(z * g->ny + y) * g->nx + x];
+    int rc = fft3(work, g->mz, g->my, g->mx, 0);
+    if (rc) return rc;
+    for (int64_t i = 0; i < Vm; ++i) work[i] *= conjugate ? conj(H[i]) : H[i];
+    rc = fft3(work, g->mz, g->my, g->mx, 1);
+    if (rc) return rc;
+    for (int64_t z = 0; z < g->nz; ++z)
+        for (int64_t y = 0; y < g->ny; ++y)
+            for (int64_t x = 0; x < g->nx; ++x)
+                out[(z * g->ny + y) * g->nx + x] = creal(work[(z * g->my + y) * g->mx + x]);
+    return 0;
+}
+
+static int same_setup(const double *psf, const int64_t n[3], const int64_t k[3], struct same_geom *g, cplx **H,
+                      cplx **work)
+{
+    g->nz = n[0]; g->ny = n[1]; g->nx = n[2];
+    g->mz = n[0] + k[0] - 1; g->my = n[1] + k[1] - 1; g->mx = n[2] + k[2] - 1;
+    int64_t Vm = g->mz * g->my * g->mx;
+    double *h0 = malloc(sizeof(double) * (size_t)Vm);
+    *H = malloc(sizeof(cplx) * (size_t)Vm);
+    *work = malloc(sizeof(cplx) * (size_t)Vm);
+    if (!h0 || !*H || !*work) { free(h0); free(*H); free(*work); *H = *work = NULL; return -2; }
+    same_embed_psf(psf, k[0], k[1], k[2], h0, g->mz, g->my, g->mx);
+    for (int64_t i = 0; i < Vm; ++i) (*H)[i] = h0[i];
+    free(h0);
+    return fft3(*H, g->mz, g->my, g->mx, 0);
+}
+
+/* b = same-mode convolution of u (image box n) with psf (box k); flipped: its adjoint. */
+int orc_conv_same(const double *psf, const double *u, double *b, int64_t nz, int64_t ny, int64_t nx, int64_t kz,
+                  int64_t ky, int64_t kx, int flipped)
+{
+    if (!psf || !u || !b || nz < 1 || ny < 1 || nx < 1 || kz < 1 || ky < 1 || kx < 1) return -1;
+    const int64_t n[3] = {nz, ny, nx}, k[3] = {kz, ky, kx};
+    struct same_geom g;
+    cplx *H, *work;
+    int rc = same_setup(psf, n, k, &g, &H, &work);
+    if (!rc) rc = same_filter(&g, H, u, b, work, flipped);
+    free(H); free(work);
+    return rc;
+}
+
+/* RL with linear boundaries: n_iter iterations from x_0 = max(mean(d), eps). */
+int orc_rl_same(const double *d, const double *psf, int64_t nz, int64_t ny, int64_t nx, int64_t kz, int64_t ky,
+                int64_t kx, int n_iter, double eps, double *out)
+{
+    if (!d || !psf || !out || nz < 1 || ny < 1 || nx < 1 || kz < 1 || ky < 1 || kx < 1 || n_iter < 0 ||
+        !(eps > 0))
+        return -1;
+    const int64_t n[3] = {nz, ny, nx}, k[3] = {kz, ky, kx};
+    int64_t V = nz * ny * nx;
+    struct same_geom g;
+    cplx *H, *work;
+    int rc = same_setup(psf, n, k, &g, &H, &work);
+    double *u = malloc(sizeof(double) * (size_t)V), *b = malloc(sizeof(double) * (size_t)V);
+    double *q = malloc(sizeof(double) * (size_t)V);
+    if (!u || !b || !q) rc = rc ? rc : -2;
+    if (!rc) {
+        double u0 = orc_initial_value(d, V, eps);
+        for (int64_t i = 0; i < V; ++i) u[i] = u0;
+        for (int it = 0; it < n_iter && !rc; ++it) {
+            rc = same_filter(&g, H, u, b, work, 0);                         /* forward conv */
+            if (rc) break;
+            for (int64_t i = 0; i < V; ++i) b[i] = d[i] / (b[i] > eps ? b[i] : eps);   /* ratio */
+            rc = same_filter(&g, H, b, q, work, 1);                          /* adjoint */
+            if (rc) break;
+            for (int64_t i = 0; i < V; ++i) u[i] *= q[i];                     /* update */
+        }
+        if (!rc) memcpy(out, u, sizeof(double) * (size_t)V);
+    }
+    free(H); free(work); free(u); free(b); free(q);
+    return rc;
+}
+
 /* Quality metrics for metric-guided stopping (the paper's Section 4 stops RL when the
  * improvement of an image-quality measure between consecutive iterations falls under a
  * threshold; Section 3 lists scale-invariant PSNR among its metrics).

@@ -685,3 +685,75 @@ def test_rl_monitor_stopping_rules():
     # checks only every third iteration
     _, n, _ = oracle.rl_monitor(d, psf, 40, 1e-6, oracle.METRIC_NLL, tol, 3, xt)
     assert n % 3 == 0 and n >= first + 1 and n - 3 < first + 1
+
+
+# ------------------------------------------------- linear ("same"-mode) boundaries
+
+def direct_same(psf, u, flipped=False):
+    """b(x) = sum_t p(t + c) u(x - t) over x - t inside the box (adjoint: u(x + t))."""
+    n, k = u.shape, psf.shape
+    c = [kk // 2 for kk in k]
+    out = np.zeros(n)
+    for x in itertools.product(*[range(v) for v in n]):
+        s = 0.0
+        for t0 in range(-c[0], k[0] - c[0]):
+            for t1 in range(-c[1], k[1] - c[1]):
+                for t2 in range(-c[2], k[2] - c[2]):
+                    y = (x[0] + t0, x[1] + t1, x[2] + t2) if flipped else (x[0] - t0, x[1] - t1, x[2] - t2)
+                    if all(0 <= y[i] < n[i] for i in range(3)):
+                        s += psf[t0 + c[0], t1 + c[1], t2 + c[2]] * u[y]
+        out[x] = s
+    return out
+
+
+@pytest.mark.parametrize("n,k", [((3, 4, 5), (3, 2, 5)), ((4, 3, 2), (5, 7, 3)), ((2, 5, 6), (1, 1, 1))])
+def test_conv_same_against_direct_loops(n, k):
+    r = np.random.default_rng(sum(n) + 10 * sum(k))
+    psf = r.uniform(0, 1, k)
+    u = r.uniform(-1, 1, n)
+    for flipped in (False, True):
+        assert np.allclose(oracle.conv_same(psf, u, flipped), direct_same(psf, u, flipped), rtol=1e-12, atol=1e-13)
+
+
+def test_conv_same_adjoint_identity():
+    r = np.random.default_rng(91)
+    psf = r.uniform(0, 1, (5, 3, 4))
+    x = r.standard_normal((6, 7, 9))
+    y = r.standard_normal((6, 7, 9))
+    lhs = np.vdot(oracle.conv_same(psf, x), y)
+    rhs = np.vdot(x, oracle.conv_same(psf, y, True))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_conv_same_equals_circular_away_from_the_border():
+    # an object with zero margins of at least the PSF's half-width never meets the border,
+    # so zero padding and wrap-around give the same blur
+    n, k = (12, 14, 16), (5, 3, 7)
+    r = np.random.default_rng(92)
+    psf = r.uniform(0, 1, k)
+    u = np.zeros(n)
+    u[3:-3, 2:-2, 4:-4] = r.uniform(0, 1, (6, 10, 8))
+    big = np.zeros(n)
+    sl = tuple(slice(nn // 2 - kk // 2, nn // 2 - kk // 2 + kk) for nn, kk in zip(n, k))
+    big[sl] = psf            # the same PSF, peak at floor(n/2) of an image-sized box
+    H = oracle.psf_spectrum(big)
+    assert np.allclose(oracle.conv_same(psf, u), oracle.convolve(H, u), atol=1e-12)
+    assert np.allclose(oracle.conv_same(psf, u, True), oracle.convolve(H, u, True), atol=1e-12)
+
+
+def test_rl_same_matches_direct_path_and_keeps_flux():
+    shape, k = (4, 5, 6), (3, 5, 3)
+    r = np.random.default_rng(93)
+    d = r.uniform(1, 20, shape)
+    psf = r.uniform(0.1, 1, k)
+    psf /= psf.sum()
+    u = np.full(shape, d.mean())
+    for _ in range(4):
+        b = direct_same(psf, u)
+        u = u * direct_same(psf, d / np.maximum(b, 1e-6), True)
+    got = oracle.rl_same(d, psf, 4, 1e-6)
+    assert np.allclose(got, u, rtol=1e-11)
+    # each step keeps the total flux (the adjoint pairs the ratio with the blur it divides)
+    assert abs(got.sum() - d.sum()) <= 1e-11 * d.sum()
+    # a 1-voxel PSF makes the first iterate the image itself
+    assert np.allclose(oracle.rl_same(d, np.array([[[0.7]]]), 1, 1e-6), d, rtol=1e-12)
