@@ -65,8 +65,8 @@ CUBIC_API const char *cubic_last_error(void);
 CUBIC_API int cubic_rl_supported_length(int64_t n);
 
 /* Create a plan for volumes of size dims = {nz, ny, nx} and PSF `psf` (device float32
- * [nz][ny][nx], peak at (nz/2, ny/2, nx/2), floor division).  Section 4 of the paper:
- * "Both the image and the PSF have the same ZYX size".  The plan moves the PSF peak to
+ * [nz][ny][nx], peak at (nz/2, ny/2, nx/2), floor division).  In Section 4 of the paper
+ * the PSF volume is as large as the image volume.  The plan moves the PSF peak to
  * the origin and keeps H = DFT3(psf shifted) / V (complex64, [nz][ny][nx/2+1] padded),
  * plus twiddle tables; the caller keeps owning `psf` and may free it once the stream
  * has passed this call.  flags: reserved, pass 0.
@@ -122,6 +122,27 @@ CUBIC_API int64_t cubic_rl_batched_graph_nodes(void);
  * allocates the two device staging volumes (released with the plan). */
 CUBIC_API cubic_status_t cubic_rl_deconvolve_host(cubic_rl_plan_t plan, const float *image, int n_iter,
                                                   float eps, float *out, void *stream);
+
+/* Create a plan with linear ("same"-mode, zero-padded) boundaries for images of size
+ * dims = {nz, ny, nx} and a PSF box psf_dims = {kz, ky, kx} (device float32, peak at
+ * floor(k/2) per axis), which may be smaller than the image.  The paper convolves
+ * same-size arrays circularly; here the estimate and the image stay on their own box, the
+ * blur sees zeros outside it, b(x) = sum_t p(t + c) u(x - t) with c = floor(k/2), and the
+ * back-projection is its adjoint.  The transforms run on the smallest supported lengths
+ * m >= max(n + floor(k/2), k) per axis, which is exact for this output.  The plan owns two
+ * zero-padded copies of the image box (image and estimate).  Supported on such a plan:
+ * cubic_rl_deconvolve, cubic_rl_deconvolve_host, cubic_rl_convolve,
+ * cubic_rl_plan_update_psf (psf of psf_dims), cubic_rl_autotune and the plan queries.
+ * Every other entry point returns INVALID_ARG for it.  Errors: INVALID_ARG,
+ * UNSUPPORTED_SIZE (no supported length, or padded nz or ny above 65535), ALIGNMENT,
+ * OUT_OF_MEMORY, CUDA. */
+CUBIC_API cubic_status_t cubic_rl_plan_linear(cubic_rl_plan_t *plan, const int64_t dims[3],
+                                              const int64_t psf_dims[3], const float *psf, unsigned flags,
+                                              void *stream);
+
+/* The image dims and the transform dims of a plan (equal unless it has linear
+ * boundaries); either pointer may be NULL. */
+CUBIC_API cubic_status_t cubic_rl_plan_dims(cubic_rl_plan_t plan, int64_t image[3], int64_t transform[3]);
 
 /* Normalised anisotropic Gaussian PSF, psf = amp * g / sum(g) with
  * g = exp(-(dx^2 + dy^2) / (2 sigma_xy^2) - dz^2 / (2 sigma_z^2)), (dx, dy, dz) = index -
@@ -305,9 +326,9 @@ CUBIC_API cubic_status_t cubic_rl_profile_read(cubic_rl_plan_t plan, int n_kinds
 
 /* ---- building blocks (the same kernels, exposed for the forward model and for tests) ---- */
 
-/* Circular convolution with the plan's PSF (Section 4 of the paper, "forward
- * convolution with the PSF"): out = psf (*) in.  flipped != 0 gives the correlation
- * with the PSF ("back-convolution with the flipped PSF"), the adjoint of the former.
+/* Circular convolution with the plan's PSF (the blur step of Section 4 of the paper):
+ * out = psf (*) in.  flipped != 0 gives the correlation with the PSF (a convolution with
+ * the mirrored PSF, the step that carries the ratio back), the adjoint of the former.
  * in, out: device float32 [nz][ny][nx]; they may alias.  Uses the plan workspace. */
 CUBIC_API cubic_status_t cubic_rl_convolve(cubic_rl_plan_t plan, const float *in, int flipped, float *out,
                                  void *stream);

@@ -10,11 +10,11 @@ method's arithmetic.
 The arithmetic lives in ``rl_oracle.c`` (plain C, double precision, optional
 OpenMP); this module compiles it with gcc on first use and wraps it with
 ctypes.  It follows the paper's Section 4 "Richardson-Lucy deconvolution":
-forward convolution with the PSF, ratio with the observed image,
-back-convolution with the flipped PSF, multiplicative update.  The readings
-taken where the paper is silent (circular boundaries, PSF centre at
-floor(n/2), u0 = max(mean(d), eps), denominator clamp max(b, eps)) are stated
-in ``rl_oracle.c``.
+each iteration blurs the estimate with the PSF, divides the measured volume by
+that blur, correlates the quotient with the PSF and multiplies the estimate by
+the result.  The readings taken where the paper is silent (circular
+boundaries, PSF centre at floor(n/2), u0 = max(mean(d), eps), denominator
+clamp max(b, eps)) are stated in ``rl_oracle.c``.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 in ``tests/test_oracle.py`` (brute-force DFT, direct convolution, closed-form

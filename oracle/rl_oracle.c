@@ -7,13 +7,12 @@
  * code, header, table or constant with the CUDA path.
  *
  * What it computes follows the paper (arXiv 2510.14143), Section 4,
- * "Richardson-Lucy deconvolution": each iteration is (1) a forward
- * convolution of the estimate with the PSF, (2) the ratio of the observed
- * image to that blurred estimate, (3) a back-convolution of the ratio with the
- * flipped PSF and (4) a multiplicative update of the estimate.  The same
- * section states that the PSF has the same ZYX size as the image and that the
- * convolutions are done with FFTs.  Where the paper is silent the oracle takes
- * these readings (each listed in the design doc):
+ * "Richardson-Lucy deconvolution": each iteration (1) blurs the estimate with
+ * the PSF, (2) divides the measured volume by that blur, (3) correlates the
+ * quotient with the PSF (convolution with the mirrored PSF) and (4) multiplies
+ * the estimate by the result.  In the same section the PSF volume is as large
+ * as the image and the convolutions run through FFTs.  Where the paper is
+ * silent the oracle takes these readings:
  *   - circular boundaries (FFT convolution of same-size arrays, no padding);
  *   - the PSF peak sits at index floor(n/2) on every axis and is moved to
  *     the origin before the transform;
@@ -370,8 +369,8 @@ int orc_rl(const double *d, const double *psf, int64_t nz, int64_t ny, int64_t n
     return rc;
 }
 
-/* RL with automatic stopping (the paper's Section 4, "automatic stopping criteria that
- * monitor image quality improvement between consecutive iterations", with a threshold).
+/* RL with automatic stopping (the paper's Section 4 ends the iteration once the gain in
+ * image quality from one iteration to the next drops under a threshold).
  * Reading: the improvement of iteration k is the relative change of the estimate,
  *   delta_k = ||u_{k+1} - u_k||_2 / ||u_k||_2,
  * checked after every check_every-th iteration (and after the last one); the run stops

@@ -8,8 +8,8 @@ kernels of ``libcubic_rl.so``; there is no CPU fallback.  If the library has
 not been built, every call raises.
 
 The method is Section 4 of arXiv 2510.14143 ("Richardson-Lucy
-deconvolution"): forward convolution with the PSF, ratio with the observed
-image, back-convolution with the flipped PSF, multiplicative update.
+deconvolution"): blur the estimate with the PSF, divide the measured volume by
+the blur, correlate the quotient with the PSF, multiply the estimate by it.
 """
 from __future__ import annotations
 
@@ -41,6 +41,9 @@ _SIGS = {
     "cubic_last_error": ([], ctypes.c_char_p),
     "cubic_rl_supported_length": ([_i64], _ci),
     "cubic_rl_plan": ([ctypes.POINTER(_vp), ctypes.POINTER(_i64), _vp, ctypes.c_uint, _vp], _ci),
+    "cubic_rl_plan_linear": ([ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp, ctypes.c_uint,
+                              _vp], _ci),
+    "cubic_rl_plan_dims": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], _ci),
     "cubic_rl_plan_update_psf": ([_vp, _vp, _vp], _ci),
     "cubic_rl_plan_destroy": ([_vp], _ci),
     "cubic_rl_workspace_bytes": ([_vp, ctypes.POINTER(_sz)], _ci),
@@ -170,9 +173,31 @@ def cubic_rl_plan(dims, psf, flags: int = 0, stream=None) -> Plan:
     return Plan(h.value, dims)
 
 
+def cubic_rl_plan_linear(dims, psf, flags: int = 0, stream=None) -> Plan:
+    """Plan with linear (zero-padded, same-mode) boundaries: image shape dims, PSF box psf.shape."""
+    import torch
+    dims = tuple(int(d) for d in dims)
+    kdims = tuple(int(k) for k in psf.shape)
+    h = _vp()
+    _check(lib().cubic_rl_plan_linear(ctypes.byref(h), (_i64 * 3)(*dims), (_i64 * 3)(*kdims),
+                                      _ptr(psf, torch.float32, kdims[0] * kdims[1] * kdims[2], "psf"), flags,
+                                      _stream(stream)), "cubic_rl_plan_linear")
+    plan = Plan(h.value, dims)
+    plan.psf_voxels = kdims[0] * kdims[1] * kdims[2]
+    return plan
+
+
+def cubic_rl_plan_dims(plan: Plan):
+    """((image nz, ny, nx), (transform nz, ny, nx))."""
+    im, tr = (_i64 * 3)(), (_i64 * 3)()
+    _check(lib().cubic_rl_plan_dims(plan.handle, im, tr), "cubic_rl_plan_dims")
+    return tuple(im), tuple(tr)
+
+
 def cubic_rl_plan_update_psf(plan: Plan, psf, stream=None) -> None:
     import torch
-    _check(lib().cubic_rl_plan_update_psf(plan.handle, _ptr(psf, torch.float32, plan.voxels, "psf"),
+    n = getattr(plan, "psf_voxels", plan.voxels)
+    _check(lib().cubic_rl_plan_update_psf(plan.handle, _ptr(psf, torch.float32, n, "psf"),
                                           _stream(stream)), "cubic_rl_plan_update_psf")
 
 

@@ -1,9 +1,9 @@
 """Differentiable Richardson-Lucy deconvolution (torch.autograd.Function).
 
 ``RLDeconvolve.apply(d, sigma_xy, sigma_z, amp, n_iter, eps, ckpt_every)`` runs
-``n_iter`` Richardson-Lucy iterations (the paper's Section 4 step: forward
-convolution with the PSF, ratio with the image, convolution with the flipped
-PSF, multiplicative update) on every volume of ``d`` ([B, Z, Y, X] or
+``n_iter`` Richardson-Lucy iterations (the paper's Section 4 step: blur by the
+PSF, quotient of the image by the blur, correlation of the quotient with the
+PSF, product with the estimate) on every volume of ``d`` ([B, Z, Y, X] or
 [Z, Y, X] float32 CUDA) with the normalised anisotropic Gaussian PSF
 ``amp * g / sum(g)`` of the given parameters, and returns the estimates.  Its
 backward returns dL/dd and dL/d(sigma_xy, sigma_z, amp).

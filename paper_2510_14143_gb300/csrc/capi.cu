@@ -233,6 +233,14 @@ struct cubic_rl_plan_s {
     bool allow_real_h = false;  // set by cubic_rl_plan (may allocate Hr)
     bool use_real_h = false;
     float *Hr = nullptr;        // [nz][ny][xp], owned
+    // linear ("same"-mode) boundaries: nz, ny, nx are then the transform's dims, the image is
+    // iz x iy x ix (V, rows count its voxels and rows), the plan keeps the image and the
+    // estimate in rows zero-padded to nx (lin: [2][iz][iy][nx]) and the spectrum work array
+    // holds iz planes
+    bool linear = false;
+    int64_t iz = 0, iy = 0, ix = 0;
+    int64_t pdims[3] = {0, 0, 0};  // the PSF box of a linear plan
+    float *lin = nullptr;
     // launch accounting and optional per-kernel CUDA-event timing
     int64_t launches[KK_COUNT] = {};
     double bytes[KK_COUNT] = {};
@@ -244,7 +252,14 @@ struct cubic_rl_plan_s {
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-static size_t spec_elems(const cubic_rl_plan_s *p) { return (size_t)p->nz * p->ny * p->xp; }
+// planes and rows per plane of the work arrays (the image's for a linear plan)
+static int64_t work_planes(const cubic_rl_plan_s *p) { return p->linear ? p->iz : p->nz; }
+static int64_t work_ny(const cubic_rl_plan_s *p) { return p->linear ? p->iy : p->ny; }
+// the spectrum work array, and H (all nz planes of the transform)
+static size_t spec_elems(const cubic_rl_plan_s *p) { return (size_t)work_planes(p) * p->ny * p->xp; }
+static size_t h_elems(const cubic_rl_plan_s *p) { return (size_t)p->nz * p->ny * p->xp; }
+// elements of one padded real work array of a linear plan
+static size_t lin_elems(const cubic_rl_plan_s *p) { return (size_t)p->iz * p->iy * p->nx; }
 
 static cubic_status_t ensure_workspace(cubic_rl_plan_s *p)
 {
@@ -328,9 +343,13 @@ static cudaError_t run_z(cubic_rl_plan_s *p, const ZArgs &a, cudaStream_t st)
     return counted(p, kind[a.mode], st, [&] { return p->kz->yzv[p->vz].z(a, st); }, bytes);
 }
 
-static YArgs y_args(const cubic_rl_plan_s *p, float2 *spec, int inverse, int64_t c0, int64_t c1)
+// full: the whole transform box (H); otherwise the work geometry, where a linear plan's Y
+// lines load their first iy rows (forward; the rest is zero padding) or store them (inverse)
+static YArgs y_args(const cubic_rl_plan_s *p, float2 *spec, int inverse, int64_t c0, int64_t c1, bool full = false)
 {
-    return YArgs{spec, p->tw_y, p->nz, p->xh, p->xp, inverse, c0, c1, p->err};
+    YArgs a{spec, p->tw_y, full ? p->nz : work_planes(p), p->xh, p->xp, inverse, c0, c1, p->err};
+    if (!full && p->linear && p->iy < p->ny) (inverse ? a.nstore : a.nload) = p->iy;
+    return a;
 }
 
 // the spectral product of a convolution (ZM_CONV) or correlation (ZM_CORR); with a real
@@ -340,33 +359,42 @@ static int conv_mode(const cubic_rl_plan_s *p, int zmode)
     return (p->use_real_h && (zmode == ZM_CONV || zmode == ZM_CORR)) ? (int)ZM_MUL_REAL : zmode;
 }
 
-static ZArgs z_args(const cubic_rl_plan_s *p, float2 *spec, int mode, float scale, int64_t c0, int64_t c1)
+// a linear plan's Z lines have iz planes of data; the rest reads as zero and is not stored
+static ZArgs z_args(const cubic_rl_plan_s *p, float2 *spec, int mode, float scale, int64_t c0, int64_t c1,
+                    bool full = false)
 {
-    return ZArgs{spec, p->H, p->tw_z, p->ny, p->xh, p->xp, conv_mode(p, mode), scale, c0, c1, p->err, p->nz,
-                 p->use_real_h ? p->Hr : nullptr};
+    ZArgs a{spec, p->H, p->tw_z, p->ny, p->xh, p->xp, conv_mode(p, mode), scale, c0, c1, p->err, p->nz,
+            p->use_real_h ? p->Hr : nullptr};
+    if (!full && p->linear && p->iz < p->nz) a.nload = a.nstore = p->iz;
+    return a;
 }
 
-static XArgs x_args(const cubic_rl_plan_s *p)
+// a linear plan's X rows are the image's (zero-padded to nx), mapped onto its spectrum rows
+static XArgs x_args(const cubic_rl_plan_s *p, bool full = false)
 {
     XArgs a{};
     a.tw = p->tw_x;
-    a.rows = p->rows;
+    a.rows = full ? p->nz * p->ny : work_planes(p) * work_ny(p);
     a.xp = p->xp;
     a.err = p->err;
+    if (!full && p->linear && p->iy < p->ny) {
+        a.ny_img = p->iy;
+        a.ny_spec = p->ny;
+    }
     return a;
 }
 
 // Forward 3D real-to-half-complex transform of `real` into `spec`, optionally
 // scaled (scale applies in the Z pass).
 static cubic_status_t enqueue_forward3(cubic_rl_plan_s *p, const float *real, float2 *spec, float scale,
-                                       cudaStream_t st)
+                                       cudaStream_t st, bool full = false)
 {
-    XArgs xa = x_args(p);
+    XArgs xa = x_args(p, full);
     xa.spec_out = spec;
     xa.src = real;
     CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
-    CUBIC_CUDA(run_y(p, y_args(p, spec, 0, 0, p->xh), st));
-    CUBIC_CUDA(run_z(p, z_args(p, spec, ZM_FWD_SCALE, scale, 0, p->xh), st));
+    CUBIC_CUDA(run_y(p, y_args(p, spec, 0, 0, p->xh, full), st));
+    CUBIC_CUDA(run_z(p, z_args(p, spec, ZM_FWD_SCALE, scale, 0, p->xh, full), st));
     return CUBIC_OK;
 }
 
@@ -412,36 +440,66 @@ __global__ void k_real_h(float2 *__restrict__ H, float *__restrict__ Hr, int64_t
     }
 }
 
+// Places the PSF box (kz, ky, kx; peak at floor(k/2)) into the zeroed transform box h0
+// (nz, ny, nx) with its peak at the origin, wrapping negative offsets: the same-mode
+// convolution's kernel on the padded box.
+__global__ void k_place_psf(const float *__restrict__ psf, int64_t kz, int64_t ky, int64_t kx,
+                            float *__restrict__ h0, int64_t nz, int64_t ny, int64_t nx)
+{
+    const int64_t K = kz * ky * kx;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i % kx, y = (i / kx) % ky, z = i / (kx * ky);
+        const int64_t zz = ((z - kz / 2) % nz + nz) % nz, yy = ((y - ky / 2) % ny + ny) % ny,
+                      xx = ((x - kx / 2) % nx + nx) % nx;
+        h0[(zz * ny + yy) * nx + xx] = psf[i];
+    }
+}
+
 static cubic_status_t load_psf(cubic_rl_plan_s *p, const float *psf, cudaStream_t st)
 {
     cubic_status_t s = ensure_workspace(p);
     if (s != CUBIC_OK) return s;
-    // the shifted real PSF fits in the workspace (xp >= nx/2+1 complex >= nx floats)
+    const int64_t Vt = p->nz * p->ny * p->nx;  // the transform box
     float *h0 = (float *)p->ws;
-    CUBIC_CUDA(counted(p, KK_SHIFT, st, [&] {
-        k_center_to_origin<<<grid_for(p->V, 256), 256, 0, st>>>(psf, h0, p->nz, p->ny, p->nx);
-        return cudaGetLastError();
-    }));
+    if (p->linear) {
+        // the work spectrum holds only the image's planes: a scratch box for h0
+        void *m = nullptr;
+        CUBIC_CUDA(cudaMallocAsync(&m, (size_t)Vt * sizeof(float), st));
+        h0 = (float *)m;
+        CUBIC_CUDA(cudaMemsetAsync(h0, 0, (size_t)Vt * sizeof(float), st));
+        CUBIC_CUDA(counted(p, KK_SHIFT, st, [&] {
+            k_place_psf<<<grid_for(p->pdims[0] * p->pdims[1] * p->pdims[2], 256), 256, 0, st>>>(
+                psf, p->pdims[0], p->pdims[1], p->pdims[2], h0, p->nz, p->ny, p->nx);
+            return cudaGetLastError();
+        }));
+    } else {
+        // the shifted real PSF fits in the workspace (xp >= nx/2+1 complex >= nx floats)
+        CUBIC_CUDA(counted(p, KK_SHIFT, st, [&] {
+            k_center_to_origin<<<grid_for(p->V, 256), 256, 0, st>>>(psf, h0, p->nz, p->ny, p->nx);
+            return cudaGetLastError();
+        }));
+    }
     bool even = false;
     if (p->allow_real_h) {
         // the reduction slot after the partial sums holds the flag for a moment
         unsigned *flag = (unsigned *)(p->partial + kReduceBlocks);
         CUBIC_CUDA(cudaMemsetAsync(flag, 0, sizeof(unsigned), st));
-        k_check_even<<<grid_for(p->V, 256), 256, 0, st>>>(h0, p->nz, p->ny, p->nx, flag);
+        k_check_even<<<grid_for(Vt, 256), 256, 0, st>>>(h0, p->nz, p->ny, p->nx, flag);
         unsigned host = 1;
         CUBIC_CUDA(cudaMemcpyAsync(&host, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         CUBIC_CUDA(cudaStreamSynchronize(st));
         even = host == 0;
     }
     p->use_real_h = false;  // H itself is complex while it is computed
-    s = enqueue_forward3(p, h0, p->H, (float)(1.0 / (double)p->V), st);
+    s = enqueue_forward3(p, h0, p->H, (float)(1.0 / (double)Vt), st, true);
+    if (p->linear) CUBIC_CUDA(cudaFreeAsync(h0, st));
     if (s != CUBIC_OK || !even) return s;
     if (!p->Hr) {
         void *m = nullptr;
-        CUBIC_CUDA(cudaMalloc(&m, spec_elems(p) * sizeof(float)));
+        CUBIC_CUDA(cudaMalloc(&m, h_elems(p) * sizeof(float)));
         p->Hr = (float *)m;
     }
-    k_real_h<<<grid_for((int64_t)spec_elems(p), 256), 256, 0, st>>>(p->H, p->Hr, (int64_t)spec_elems(p));
+    k_real_h<<<grid_for((int64_t)h_elems(p), 256), 256, 0, st>>>(p->H, p->Hr, (int64_t)h_elems(p));
     CUBIC_CUDA(cudaGetLastError());
     p->use_real_h = true;
     return CUBIC_OK;
@@ -505,27 +563,10 @@ static void tune_store(const cubic_rl_plan_s *p)
     fclose(f);
 }
 
-extern "C" cubic_status_t cubic_rl_plan(cubic_rl_plan_t *plan, const int64_t dims[3], const float *psf,
-                                        unsigned flags, void *stream)
+// Allocations, twiddles and H of a plan whose dims (and, for a linear plan, image dims and
+// PSF box) are set; destroys it on failure.
+static cubic_status_t plan_build(cubic_rl_plan_s *p, const float *psf, cudaStream_t st, cubic_rl_plan_t *plan)
 {
-    if (!plan || !dims || !psf) return fail(CUBIC_ERR_INVALID_ARG, "plan, dims and psf must be non-null");
-    *plan = nullptr;
-    if (flags != 0) return fail(CUBIC_ERR_INVALID_ARG, "flags must be 0");
-    for (int i = 0; i < 3; ++i)
-        if (dims[i] < 1 || !find_axis(dims[i]))
-            return fail(CUBIC_ERR_UNSUPPORTED_SIZE, "axis %d has unsupported length %lld", i, (long long)dims[i]);
-    if (!aligned16(psf)) return fail(CUBIC_ERR_ALIGNMENT, "psf must be 16-byte aligned");
-    if (dims[0] > 65535 || dims[1] > 65535)
-        return fail(CUBIC_ERR_UNSUPPORTED_SIZE, "nz and ny must be <= 65535");
-
-    cubic_rl_plan_s *p = new (std::nothrow) cubic_rl_plan_s();
-    if (!p) return fail(CUBIC_ERR_OUT_OF_MEMORY, "host allocation failed");
-    cudaStream_t st = (cudaStream_t)stream;
-    p->nz = dims[0];
-    p->ny = dims[1];
-    p->nx = dims[2];
-    p->V = p->nz * p->ny * p->nx;
-    p->rows = p->nz * p->ny;
     p->xh = p->nx / 2 + 1;
     p->xp = (p->xh + 15) / 16 * 16;
     p->kx = find_axis(p->nx);
@@ -541,7 +582,7 @@ extern "C" cubic_status_t cubic_rl_plan(cubic_rl_plan_t *plan, const int64_t dim
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return bail(fail(CUBIC_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
     void *mem = nullptr;
-    e = cudaMalloc(&mem, spec_elems(p) * sizeof(float2));
+    e = cudaMalloc(&mem, h_elems(p) * sizeof(float2));
     if (e != cudaSuccess) return bail(fail(CUBIC_ERR_OUT_OF_MEMORY, "H: %s", cudaGetErrorString(e)));
     p->H = (float2 *)mem;
     const int64_t ntw = p->nx + p->ny + p->nz;
@@ -559,6 +600,11 @@ extern "C" cubic_status_t cubic_rl_plan(cubic_rl_plan_t *plan, const int64_t dim
     p->err = (unsigned *)mem;
     e = cudaMemsetAsync(p->err, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return bail(fail(CUBIC_ERR_CUDA, "error word: %s", cudaGetErrorString(e)));
+    if (p->linear) {
+        e = cudaMalloc(&mem, 2 * lin_elems(p) * sizeof(float));
+        if (e != cudaSuccess) return bail(fail(CUBIC_ERR_OUT_OF_MEMORY, "padded arrays: %s", cudaGetErrorString(e)));
+        p->lin = (float *)mem;
+    }
     tuned_variants(p);
 
     k_twiddles<<<grid_for(p->nx, 128, 1 << 20), 128, 0, st>>>(p->tw_x, (int)p->nx);
@@ -569,6 +615,83 @@ extern "C" cubic_status_t cubic_rl_plan(cubic_rl_plan_t *plan, const int64_t dim
     s = load_psf(p, psf, st);
     if (s != CUBIC_OK) return bail(s);
     *plan = p;
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_rl_plan(cubic_rl_plan_t *plan, const int64_t dims[3], const float *psf,
+                                        unsigned flags, void *stream)
+{
+    if (!plan || !dims || !psf) return fail(CUBIC_ERR_INVALID_ARG, "plan, dims and psf must be non-null");
+    *plan = nullptr;
+    if (flags != 0) return fail(CUBIC_ERR_INVALID_ARG, "flags must be 0");
+    for (int i = 0; i < 3; ++i)
+        if (dims[i] < 1 || !find_axis(dims[i]))
+            return fail(CUBIC_ERR_UNSUPPORTED_SIZE, "axis %d has unsupported length %lld", i, (long long)dims[i]);
+    if (!aligned16(psf)) return fail(CUBIC_ERR_ALIGNMENT, "psf must be 16-byte aligned");
+    if (dims[0] > 65535 || dims[1] > 65535)
+        return fail(CUBIC_ERR_UNSUPPORTED_SIZE, "nz and ny must be <= 65535");
+
+    cubic_rl_plan_s *p = new (std::nothrow) cubic_rl_plan_s();
+    if (!p) return fail(CUBIC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    p->nz = dims[0];
+    p->ny = dims[1];
+    p->nx = dims[2];
+    p->V = p->nz * p->ny * p->nx;
+    p->rows = p->nz * p->ny;
+    return plan_build(p, psf, (cudaStream_t)stream, plan);
+}
+
+// smallest supported transform length >= n (0: none)
+static int64_t supported_at_least(int64_t n)
+{
+    for (int i = 0; i < kNumLengths; ++i)
+        if (kLengths[i] >= n) return kLengths[i];
+    return 0;
+}
+
+extern "C" cubic_status_t cubic_rl_plan_linear(cubic_rl_plan_t *plan, const int64_t dims[3],
+                                               const int64_t psf_dims[3], const float *psf, unsigned flags,
+                                               void *stream)
+{
+    if (!plan || !dims || !psf_dims || !psf) return fail(CUBIC_ERR_INVALID_ARG, "plan, dims, psf_dims, psf must be non-null");
+    *plan = nullptr;
+    if (flags != 0) return fail(CUBIC_ERR_INVALID_ARG, "flags must be 0");
+    if (!aligned16(psf)) return fail(CUBIC_ERR_ALIGNMENT, "psf must be 16-byte aligned");
+    int64_t m[3];
+    for (int i = 0; i < 3; ++i) {
+        if (dims[i] < 1 || psf_dims[i] < 1) return fail(CUBIC_ERR_INVALID_ARG, "dims and psf_dims must be >= 1");
+        // "same" output reaches floor(k/2) past each edge; a box at least as long as the
+        // PSF keeps its offsets from wrapping onto each other
+        const int64_t need = std::max(dims[i] + psf_dims[i] / 2, psf_dims[i]);
+        m[i] = supported_at_least(need);
+        if (m[i] == 0)
+            return fail(CUBIC_ERR_UNSUPPORTED_SIZE, "axis %d: no supported transform length >= %lld", i, (long long)need);
+    }
+    if (m[0] > 65535 || m[1] > 65535) return fail(CUBIC_ERR_UNSUPPORTED_SIZE, "nz and ny must be <= 65535");
+    cubic_rl_plan_s *p = new (std::nothrow) cubic_rl_plan_s();
+    if (!p) return fail(CUBIC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    p->linear = true;
+    p->iz = dims[0];
+    p->iy = dims[1];
+    p->ix = dims[2];
+    for (int i = 0; i < 3; ++i) p->pdims[i] = psf_dims[i];
+    p->nz = m[0];
+    p->ny = m[1];
+    p->nx = m[2];
+    p->V = p->iz * p->iy * p->ix;
+    p->rows = p->iz * p->iy;
+    return plan_build(p, psf, (cudaStream_t)stream, plan);
+}
+
+extern "C" cubic_status_t cubic_rl_plan_dims(cubic_rl_plan_t plan, int64_t image[3], int64_t transform[3])
+{
+    if (!plan) return fail(CUBIC_ERR_INVALID_ARG, "plan must be non-null");
+    const int64_t im[3] = {plan->linear ? plan->iz : plan->nz, plan->linear ? plan->iy : plan->ny,
+                           plan->linear ? plan->ix : plan->nx};
+    for (int i = 0; i < 3; ++i) {
+        if (image) image[i] = im[i];
+        if (transform) transform[i] = i == 0 ? plan->nz : i == 1 ? plan->ny : plan->nx;
+    }
     return CUBIC_OK;
 }
 
@@ -598,6 +721,7 @@ extern "C" cubic_status_t cubic_rl_plan_destroy(cubic_rl_plan_t plan)
     cudaFree(plan->auto_delta);
     cudaFree(plan->acc);
     cudaFree(plan->mon);
+    cudaFree(plan->lin);
     for (cudaEvent_t e : plan->ev) cudaEventDestroy(e);
     delete plan;
     return CUBIC_OK;
@@ -654,10 +778,115 @@ static cubic_status_t enqueue_init(cubic_rl_plan_s *p, const float *image, float
     return CUBIC_OK;
 }
 
+// ------------------------------------------------------------------ linear boundaries
+// A linear plan runs the same passes on rows zero-padded to the transform length: the
+// padded image has d = 0 there, so r = 0 there, and the estimate starts and stays at 0
+// there (u q with u = 0), which is exactly "same"-mode convolution with zero padding.
+
+// rows of nin values -> rows of nout >= nin values, zero past nin
+__global__ void k_pad_rows(const float *__restrict__ in, float *__restrict__ out, int64_t rows, int64_t nin,
+                           int64_t nout)
+{
+    const int64_t n = rows * nout;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / nout, x = i - r * nout;
+        out[i] = x < nin ? in[r * nin + x] : 0.f;
+    }
+}
+
+// rows of nin values -> their first nout values
+__global__ void k_crop_rows(const float *__restrict__ in, float *__restrict__ out, int64_t rows, int64_t nin,
+                            int64_t nout)
+{
+    const int64_t n = rows * nout;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / nout, x = i - r * nout;
+        out[i] = in[r * nin + x];
+    }
+}
+
+// x_0 = max(sum / V, eps) on the first nvalid values of each padded row, 0 past them
+__global__ void k_fill_padded(float *__restrict__ u, int64_t rows, int64_t nvalid, int64_t n,
+                              const double *__restrict__ sum, int64_t V, float eps)
+{
+    const double m = sum[0] / (double)V;
+    const float v = m > (double)eps ? (float)m : eps;
+    const int64_t total = rows * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        u[i] = (i % n) < nvalid ? v : 0.f;
+}
+
+static cubic_status_t lin_pad(cubic_rl_plan_s *p, const float *in, float *out_padded, cudaStream_t st)
+{
+    const int64_t R = p->iz * p->iy, E = (int64_t)lin_elems(p);
+    CUBIC_CUDA(counted(p, KK_SHIFT, st, [&] {
+        k_pad_rows<<<grid_for(E, 256), 256, 0, st>>>(in, out_padded, R, p->ix, p->nx);
+        return cudaGetLastError();
+    }, 4.0 * (double)(p->V + E)));
+    return CUBIC_OK;
+}
+
+static cubic_status_t lin_crop(cubic_rl_plan_s *p, const float *padded, float *out, cudaStream_t st)
+{
+    const int64_t R = p->iz * p->iy;
+    CUBIC_CUDA(counted(p, KK_SHIFT, st, [&] {
+        k_crop_rows<<<grid_for(p->V, 256), 256, 0, st>>>(padded, out, R, p->nx, p->ix);
+        return cudaGetLastError();
+    }, 8.0 * (double)p->V));
+    return CUBIC_OK;
+}
+
+static cubic_status_t enqueue_yzy(cubic_rl_plan_s *p, float2 *spec, int zmode, cudaStream_t st);
+
+// RL of a linear plan: the image and the estimate live in the plan's padded arrays
+static cubic_status_t enqueue_rl_linear(cubic_rl_plan_s *p, const float *image, int n_iter, float eps, float *out,
+                                       float2 *spec, cudaStream_t st)
+{
+    float *dp = p->lin, *up = p->lin + lin_elems(p);
+    const int64_t R = p->iz * p->iy, E = (int64_t)lin_elems(p);
+    cubic_status_t s = lin_pad(p, image, dp, st);
+    if (s != CUBIC_OK) return s;
+    // the mean over the image's voxels: the zero padding adds nothing to the sum
+    CUBIC_CUDA(counted(p, KK_SUM, st, [&] {
+        k_sum_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(dp, E, p->partial);
+        k_sum_final<<<1, kReduceThreads, 0, st>>>(p->partial, kReduceBlocks, p->partial + kReduceBlocks);
+        return cudaGetLastError();
+    }));
+    CUBIC_CUDA(counted(p, KK_FILL, st, [&] {
+        k_fill_padded<<<grid_for(E, 256), 256, 0, st>>>(up, R, p->ix, p->nx, p->partial + kReduceBlocks, p->V, eps);
+        return cudaGetLastError();
+    }));
+    if (n_iter > 0) {
+        XArgs xa = x_args(p);
+        xa.spec_in = spec;
+        xa.spec_out = spec;
+        xa.src = up;
+        xa.u = up;
+        xa.dst = up;
+        xa.d = dp;
+        xa.eps = eps;
+        CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
+        for (int k = 0; k < n_iter; ++k) {
+            if ((s = enqueue_yzy(p, spec, ZM_CONV, st)) != CUBIC_OK) return s;
+            CUBIC_CUDA(run_x(p, XM_RATIO, xa, st));
+            if ((s = enqueue_yzy(p, spec, ZM_CORR, st)) != CUBIC_OK) return s;
+            CUBIC_CUDA(run_x(p, k + 1 < n_iter ? XM_UPDATE : XM_FINAL, xa, st));
+        }
+    }
+    return lin_crop(p, up, out, st);
+}
+
+static cubic_status_t no_linear(const cubic_rl_plan_s *p, const char *what)
+{
+    return p->linear ? fail(CUBIC_ERR_INVALID_ARG, "%s is not available for linear-boundary plans", what)
+                     : CUBIC_OK;
+}
+
 // The n_iter-iteration sequence, enqueued on `st`.
 static cubic_status_t enqueue_rl(cubic_rl_plan_s *p, const float *image, int n_iter, float eps, float *out,
                                  float2 *spec, cudaStream_t st)
 {
+    if (p->linear) return enqueue_rl_linear(p, image, n_iter, eps, out, spec, st);
     cubic_status_t s0 = enqueue_init(p, image, eps, out, st);
     if (s0 != CUBIC_OK) return s0;
     if (n_iter == 0) return CUBIC_OK;
@@ -710,9 +939,15 @@ extern "C" cubic_status_t cubic_rl_convolve(cubic_rl_plan_t plan, const float *i
     xa.spec_out = plan->ws;
     xa.src = in;
     xa.dst = out;
+    if (plan->linear) {  // through the padded arrays
+        if ((s = lin_pad(plan, in, plan->lin, st)) != CUBIC_OK) return s;
+        xa.src = plan->lin;
+        xa.dst = plan->lin + lin_elems(plan);
+    }
     CUBIC_CUDA(run_x(plan, XM_FWD, xa, st));
     if ((s = enqueue_yzy(plan, plan->ws, flipped ? ZM_CORR : ZM_CONV, st)) != CUBIC_OK) return s;
     CUBIC_CUDA(run_x(plan, XM_INV, xa, st));
+    if (plan->linear) return lin_crop(plan, plan->lin + lin_elems(plan), out, st);
     return CUBIC_OK;
 }
 
@@ -727,6 +962,7 @@ extern "C" cubic_status_t cubic_rl_spectrum_layout(cubic_rl_plan_t plan, int64_t
 extern "C" cubic_status_t cubic_rl_fft3_forward(cubic_rl_plan_t plan, const float *in, void *spec, void *stream)
 {
     if (!plan || !in || !spec) return fail(CUBIC_ERR_INVALID_ARG, "plan, in and spec must be non-null");
+    if (cubic_status_t g = no_linear(plan, "the spectrum entry point")) return g;
     if (!aligned16(in) || !aligned16(spec)) return fail(CUBIC_ERR_ALIGNMENT, "in and spec must be 16-byte aligned");
     return enqueue_forward3(plan, in, (float2 *)spec, 1.f, (cudaStream_t)stream);
 }
@@ -734,6 +970,7 @@ extern "C" cubic_status_t cubic_rl_fft3_forward(cubic_rl_plan_t plan, const floa
 extern "C" cubic_status_t cubic_rl_fft3_inverse(cubic_rl_plan_t plan, void *spec, float *out, void *stream)
 {
     if (!plan || !out || !spec) return fail(CUBIC_ERR_INVALID_ARG, "plan, spec and out must be non-null");
+    if (cubic_status_t g = no_linear(plan, "the spectrum entry point")) return g;
     if (!aligned16(out) || !aligned16(spec)) return fail(CUBIC_ERR_ALIGNMENT, "out and spec must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     float2 *sp = (float2 *)spec;
@@ -972,10 +1209,18 @@ extern "C" cubic_status_t cubic_rl_autotune(cubic_rl_plan_t plan, const float *i
     const bool prof = plan->prof;
     plan->prof = false;
     float2 *ws = plan->ws;
+    // a linear plan tunes on its padded arrays
+    const float *img_w = plan->linear ? plan->lin : image;
+    float *out_w = plan->linear ? plan->lin + lin_elems(plan) : out;
+    const size_t nw = plan->linear ? lin_elems(plan) : (size_t)plan->V;
     // every timed run starts from the spectrum of the image and a copy of it as estimate
     auto prepare = [&]() -> cubic_status_t {
-        CUBIC_CUDA(cudaMemcpyAsync(out, image, (size_t)plan->V * sizeof(float), cudaMemcpyDeviceToDevice, st));
-        return enqueue_forward3(plan, image, ws, 1.f / (float)plan->V, st);
+        if (plan->linear) {
+            cubic_status_t sp = lin_pad(plan, image, plan->lin, st);
+            if (sp != CUBIC_OK) return sp;
+        }
+        CUBIC_CUDA(cudaMemcpyAsync(out_w, img_w, nw * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        return enqueue_forward3(plan, img_w, ws, 1.f / (float)plan->V, st);
     };
     auto nothing = []() -> cubic_status_t { return CUBIC_OK; };
     float best, ms;
@@ -987,8 +1232,8 @@ extern "C" cubic_status_t cubic_rl_autotune(cubic_rl_plan_t plan, const float *i
         XArgs xa = x_args(plan);
         xa.spec_in = ws;
         xa.spec_out = ws;
-        xa.u = out;
-        xa.d = image;
+        xa.u = out_w;
+        xa.d = img_w;
         xa.eps = 1.f;
         s = time_best(st, prepare, [&]() -> cubic_status_t {
             CUBIC_CUDA(run_x(plan, XM_RATIO, xa, st));
@@ -1029,6 +1274,7 @@ extern "C" cubic_status_t cubic_rl_autotune(cubic_rl_plan_t plan, const float *i
     plan->vz = bz;
     plan->prof = prof;
     if (s == CUBIC_OK) s = prepare();  // leave finite data behind
+    if (s == CUBIC_OK && plan->linear) s = lin_crop(plan, out_w, out, st);
     if (s != CUBIC_OK) return s;
     tune_store(plan);
     return CUBIC_OK;
@@ -1216,6 +1462,7 @@ extern "C" cubic_status_t cubic_rl_deconvolve_ckpt(cubic_rl_plan_t plan, const f
                                                    int ckpt_every, float *ckpts, float *out, void *stream)
 {
     if (!plan || !image || !out || !ckpts) return fail(CUBIC_ERR_INVALID_ARG, "null pointer");
+    if (cubic_status_t g = no_linear(plan, "the differentiable path")) return g;
     if (n_iter < 1 || ckpt_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "n_iter and ckpt_every must be >= 1");
     if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
     if (!aligned16(image) || !aligned16(out) || !aligned16(ckpts))
@@ -1264,6 +1511,7 @@ extern "C" cubic_status_t cubic_rl_backward(cubic_rl_plan_t plan, const float *i
                                             float *grad_image, float *grad_psf, int accumulate_psf, void *stream)
 {
     if (!plan || !image || !ckpts || !grad_out) return fail(CUBIC_ERR_INVALID_ARG, "null pointer");
+    if (cubic_status_t g = no_linear(plan, "the differentiable path")) return g;
     if (n_iter < 1 || ckpt_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "n_iter and ckpt_every must be >= 1");
     if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
     if (!aligned16(image) || !aligned16(ckpts) || !aligned16(grad_out) || (grad_image && !aligned16(grad_image)) ||
@@ -1508,6 +1756,7 @@ extern "C" cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const f
                                                    double *history, void *stream)
 {
     if (!plan || !image || !out || !n_done) return fail(CUBIC_ERR_INVALID_ARG, "plan, image, out, n_done must be non-null");
+    if (cubic_status_t g = no_linear(plan, "automatic stopping")) return g;
     if (max_iter < 1 || check_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "max_iter and check_every must be >= 1");
     if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
     if (!(tol >= 0.f) || !(tol < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "tol must be finite and >= 0");
@@ -1649,6 +1898,7 @@ extern "C" cubic_status_t cubic_rl_deconvolve_accel(cubic_rl_plan_t plan, const 
                                                     float *out, float *alpha, void *stream)
 {
     if (!plan || !image || !out) return fail(CUBIC_ERR_INVALID_ARG, "plan, image and out must be non-null");
+    if (cubic_status_t g = no_linear(plan, "accelerated RL")) return g;
     if (n_iter < 0) return fail(CUBIC_ERR_INVALID_ARG, "n_iter must be >= 0");
     if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
     if (!aligned16(image) || !aligned16(out)) return fail(CUBIC_ERR_ALIGNMENT, "image and out must be 16-byte aligned");
@@ -1831,6 +2081,7 @@ extern "C" cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, cons
                                                       float *out, int *n_done, double *history, void *stream)
 {
     if (!plan || !image || !out || !n_done) return fail(CUBIC_ERR_INVALID_ARG, "plan, image, out, n_done must be non-null");
+    if (cubic_status_t g = no_linear(plan, "metric-guided stopping")) return g;
     if (max_iter < 1 || check_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "max_iter and check_every must be >= 1");
     if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
     if (!(tol >= -INFINITY) || tol != tol) return fail(CUBIC_ERR_INVALID_ARG, "tol must not be NaN");
@@ -2004,6 +2255,7 @@ extern "C" cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const 
                                     void *stream)
 {
     if (!plan || !a || !b || !fsc) return fail(CUBIC_ERR_INVALID_ARG, "plan, a, b and fsc must be non-null");
+    if (cubic_status_t g = no_linear(plan, "FSC")) return g;
     if (n_shells < 1 || n_shells > kFscMaxShells)
         return fail(CUBIC_ERR_INVALID_ARG, "n_shells must be in [1, %d]", kFscMaxShells);
     if (!aligned16(a) || !aligned16(b)) return fail(CUBIC_ERR_ALIGNMENT, "a and b must be 16-byte aligned");
@@ -2200,6 +2452,7 @@ extern "C" cubic_status_t cubic_rl_deconvolve_batched(const cubic_rl_plan_t *pla
     if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
     for (int v = 0; v < n; ++v) {
         if (!plans[v] || !images[v] || !outs[v]) return fail(CUBIC_ERR_INVALID_ARG, "volume %d: null pointer", v);
+        if (cubic_status_t g = no_linear(plans[v], "batched deconvolution")) return g;
         if (!aligned16(images[v]) || !aligned16(outs[v]))
             return fail(CUBIC_ERR_ALIGNMENT, "volume %d: image and out must be 16-byte aligned", v);
         if (overlaps(images[v], outs[v], (size_t)plans[v]->V * sizeof(float)))

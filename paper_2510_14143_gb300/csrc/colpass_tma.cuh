@@ -30,6 +30,7 @@ struct ColArgs {
     int mode;            // Y: 0 forward, 1 inverse.  Z: a ZMode
     float scale;         // ZM_FWD_SCALE / ZM_INV_SCALE
     unsigned *err;
+    int nstore;          // line rows stored (boxes starting at or past it are skipped); N: all
 };
 
 // largest divisor of n that is <= 256 (TMA box extent limit)
@@ -258,10 +259,13 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
         if (threadIdx.x == 0) {
             int cx, o;
             coords(tile, cx, o);
-            for (int j = 0; j < NB; ++j) {
+            // the Y pass stores through its own map (tm_h, unused for H there), whose
+            // extent can stop short of the loads'; boxes past it are not issued and the
+            // tensor map clips the one that straddles it
+            for (int j = 0; j < NB && j * R < a.nstore; ++j) {
                 const float2 *src = buf + (size_t)j * R * B;
                 if (KIND == COL_Y)
-                    tma_store_3d(&tm_spec, cx, j * R, o, src);
+                    tma_store_3d(&tm_h, cx, j * R, o, src);
                 else
                     tma_store_3d(&tm_spec, cx, o, j * R, src);
             }

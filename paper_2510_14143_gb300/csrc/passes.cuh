@@ -72,6 +72,9 @@ struct XArgs {
     // c = max(b, eps), into the compensated pair nll_stats[2 s], nll_stats[2 s + 1]
     // (value = hi + lo), s = one of 64 slots
     float *nll_stats;
+    // linear-boundary plans (0: none): image row r = z * ny_img + y is spectrum row
+    // z * ny_spec + y (the spectrum's planes have ny_spec >= ny_img rows)
+    int64_t ny_img, ny_spec;
 };
 
 struct YArgs {
@@ -84,6 +87,9 @@ struct YArgs {
     int64_t col0;  // first column of this launch (multiple of the tile width)
     int64_t col1;  // one past the last column (<= xh)
     unsigned *err;
+    // linear-boundary plans: rows of each line that are loaded (the rest reads as zero)
+    // and stored; 0: all N
+    int64_t nload, nstore;
 };
 
 // ZM_MUL_REAL: product with a real H (point-symmetric PSF), where convolution and
@@ -104,6 +110,9 @@ struct ZArgs {
     unsigned *err;
     int64_t nz;    // lines are this long (TMA path builds its tensor map from it)
     const float *Hr;  // real H, float [nz][ny][xp] (ZM_MUL_REAL)
+    // linear-boundary plans: planes of the spectrum array that are loaded (the rest of each
+    // line reads as zero) and stored; H keeps all N planes.  0: all N
+    int64_t nload, nstore;
 };
 
 // ------------------------------------------------------------------ X pass
@@ -235,6 +244,13 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     const int64_t m = block * L + l;
     const int64_t r0 = 2 * m, r1 = 2 * m + 1;
     const bool ok0 = r0 < a.rows, ok1 = r1 < a.rows;
+    // image row -> spectrum row (row indices stay below 2^32: nz, ny <= 65535)
+    auto srow = [&](int64_t r) -> int64_t {
+        if (a.ny_img <= 0) return r;
+        const unsigned q = (unsigned)r / (unsigned)a.ny_img;
+        return (int64_t)q * a.ny_spec + ((unsigned)r - q * (unsigned)a.ny_img);
+    };
+    const int64_t srow0 = srow(r0), srow1 = srow(r1);  // before the transforms need the registers
     float2 *lpair = xch + l * x_smem_line<N, P>();
     SmemPadded<x_first_radix<N, P>()> sm{lpair};
     auto sync = [] { __syncthreads(); };
@@ -258,7 +274,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             const int nr = (int)(left < 2 * L ? left : 2 * L);
             mbar_arrive_expect_tx(&bar[1], (unsigned)(nr * XB * sizeof(float2)));
             for (int r = 0; r < nr; ++r)
-                bulk_g2s(xch + (r >> 1) * x_smem_line<N, P>() + (r & 1) * XB, a.spec_in + (row0 + r) * a.xp,
+                bulk_g2s(xch + (r >> 1) * x_smem_line<N, P>() + (r & 1) * XB, a.spec_in + srow(row0 + r) * a.xp,
                          (unsigned)(XB * sizeof(float2)), &bar[1]);
         }
     }
@@ -467,7 +483,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             sm.at(t + P * i) = v[i];
         });
         sync();
-        float2 *q0 = a.spec_out + r0 * a.xp, *q1 = a.spec_out + r1 * a.xp;
+        float2 *q0 = a.spec_out + srow0 * a.xp, *q1 = a.spec_out + srow1 * a.xp;
         static_for<0, E>([&](auto i_) {
             constexpr int i = CUBIC_CI(i_);
             const int k = t + P * i;
@@ -544,16 +560,19 @@ __device__ __forceinline__ void y_body(const YArgs &a, const int64_t bx, const i
     pdl_wait();
     float2 v[E];
     const float sgn = a.inverse ? -1.f : 1.f;
+    const int nl = a.nload > 0 ? (int)a.nload : N, ns = a.nstore > 0 ? (int)a.nstore : N;
     static_for<0, E>([&](auto i_) {
         constexpr int i = CUBIC_CI(i_);
-        float2 x = ok ? base[(int64_t)(t + P * i) * a.xp] : make_float2(0.f, 0.f);
+        const int pos = t + P * i;
+        float2 x = (ok && pos < nl) ? base[(int64_t)pos * a.xp] : make_float2(0.f, 0.f);
         v[i] = make_float2(x.x, sgn * x.y);
     });
     FFT::forward(v, sm, stw, t, sync);
     if (ok) {
         static_for<0, E>([&](auto i_) {
             constexpr int i = CUBIC_CI(i_);
-            base[(int64_t)(t + P * i) * a.xp] = make_float2(v[i].x, sgn * v[i].y);
+            const int pos = t + P * i;
+            if (pos < ns) base[(int64_t)pos * a.xp] = make_float2(v[i].x, sgn * v[i].y);
         });
     }
 }
@@ -601,9 +620,11 @@ __device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const i
     pdl_wait();
     float2 v[E];
     const bool inv_only = a.mode == ZM_INV_SCALE;
+    const int nl = a.nload > 0 ? (int)a.nload : N, ns = a.nstore > 0 ? (int)a.nstore : N;
     static_for<0, E>([&](auto i_) {
         constexpr int i = CUBIC_CI(i_);
-        const float2 x = ok ? base[(int64_t)(t + P * i) * zstride] : make_float2(0.f, 0.f);
+        const int pos = t + P * i;
+        const float2 x = (ok && pos < nl) ? base[(int64_t)pos * zstride] : make_float2(0.f, 0.f);
         v[i] = inv_only ? cconj(x) : x;
     });
     FFT::forward(v, sm, stw, t, sync);
@@ -612,7 +633,8 @@ __device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const i
         if (ok) {
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
-                base[(int64_t)(t + P * i) * zstride] = make_float2(v[i].x * s, v[i].y * sy);
+                const int pos = t + P * i;
+                if (pos < ns) base[(int64_t)pos * zstride] = make_float2(v[i].x * s, v[i].y * sy);
             });
         }
         return;
@@ -640,7 +662,8 @@ __device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const i
     if (ok) {
         static_for<0, E>([&](auto i_) {
             constexpr int i = CUBIC_CI(i_);
-            base[(int64_t)(t + P * i) * zstride] = cconj(v[i]);
+            const int pos = t + P * i;
+            if (pos < ns) base[(int64_t)pos * zstride] = cconj(v[i]);
         });
     }
 }

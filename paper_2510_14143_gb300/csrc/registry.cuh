@@ -139,13 +139,16 @@ struct AxisShape {
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();  // defined in capi.cu
 
-// Tensor map over a [nz][ny][xp] complex array viewed as float32 [nz][ny][2 xp].
+// Tensor map over a [nz][ny][xp] complex array viewed as float32 [nz][ny][2 xp].  The
+// extents along y and z may stop short of the array (ny_ext <= ny, nz_ext <= nz): loads
+// past them read zeros and stores past them are dropped.
 inline cudaError_t encode_spectrum_map(CUtensorMap *tm, const void *base, int64_t nz, int64_t ny, int64_t xp,
-                                       int box0, int box1, int box2)
+                                       int box0, int box1, int box2, int64_t ny_ext = 0, int64_t nz_ext = 0)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
-    const cuuint64_t dims[3] = {(cuuint64_t)(2 * xp), (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * xp), (cuuint64_t)(ny_ext > 0 ? ny_ext : ny),
+                                (cuuint64_t)(nz_ext > 0 ? nz_ext : nz)};
     const cuuint64_t strides[2] = {(cuuint64_t)(2 * xp * sizeof(float)), (cuuint64_t)(2 * xp * ny * sizeof(float))};
     const cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, (cuuint32_t)box2};
     const cuuint32_t estr[3] = {1, 1, 1};
@@ -169,10 +172,13 @@ int col_grid_cap()
     return cap;
 }
 
+// nload / nstore: rows of each line loaded / stored (0: all N).  Y: rows along y of a
+// spectrum array of nz planes of ny = N rows.  Z: planes of a spectrum array holding
+// nload planes (loads and stores both stop there); H always has N planes.
 template <int N, int P, int B, int KIND, int NS, bool HREAL = false>
 cudaError_t launch_col(const float2 *spec, const float2 *H, const float *Hr, int64_t nz, int64_t ny, int64_t xp,
                        int64_t col0, int64_t col1, int64_t outer, const float2 *tw, int mode, float scale,
-                       unsigned *err, cudaStream_t st)
+                       unsigned *err, cudaStream_t st, int64_t nload = 0, int64_t nstore = 0)
 {
     constexpr int R = box_rows(N);
     constexpr size_t smem = col_smem_bytes<N, P, B, KIND, NS, HREAL>();
@@ -180,9 +186,12 @@ cudaError_t launch_col(const float2 *spec, const float2 *H, const float *Hr, int
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (col0 % B != 0) return cudaErrorInvalidValue;
+    const int64_t nl = nload > 0 ? nload : N, ns = nstore > 0 ? nstore : N;
+    if (nl > N || ns > N || (KIND == COL_Z && ns != nl)) return cudaErrorInvalidValue;
     CUtensorMap tm_spec, tm_h;
-    cudaError_t e = (KIND == COL_Y) ? encode_spectrum_map(&tm_spec, spec, nz, ny, xp, 2 * B, R, 1)
-                                    : encode_spectrum_map(&tm_spec, spec, nz, ny, xp, 2 * B, 1, R);
+    // Z: the spectrum array itself holds nl planes
+    cudaError_t e = (KIND == COL_Y) ? encode_spectrum_map(&tm_spec, spec, nz, ny, xp, 2 * B, R, 1, nl)
+                                    : encode_spectrum_map(&tm_spec, spec, nl, ny, xp, 2 * B, 1, R);
     if (e != cudaSuccess) return e;
     if (KIND == COL_Z && mode == ZM_MUL_REAL && Hr) {
         // real H: float32 [nz][ny][xp], boxes of B floats
@@ -199,6 +208,9 @@ cudaError_t launch_col(const float2 *spec, const float2 *H, const float *Hr, int
     } else if (KIND == COL_Z && H) {
         e = encode_spectrum_map(&tm_h, H, nz, ny, xp, 2 * B, 1, R);
         if (e != cudaSuccess) return e;
+    } else if (KIND == COL_Y && ns != nl) {
+        e = encode_spectrum_map(&tm_h, spec, nz, ny, xp, 2 * B, R, 1, ns);  // the store map
+        if (e != cudaSuccess) return e;
     } else {
         tm_h = tm_spec;
     }
@@ -210,6 +222,7 @@ cudaError_t launch_col(const float2 *spec, const float2 *H, const float *Hr, int
     c.mode = mode;
     c.scale = scale;
     c.err = err;
+    c.nstore = (int)ns;
     if (c.ntiles == 0) return cudaSuccess;
     const int64_t cap = col_grid_cap<N, P, B, KIND, NS, HREAL>();
     const unsigned grid = (unsigned)(c.ntiles < cap ? c.ntiles : cap);
@@ -220,7 +233,7 @@ template <int N, int P, int B, int NS>
 cudaError_t launch_y_tma(const YArgs &a, cudaStream_t st)
 {
     return launch_col<N, P, B, COL_Y, NS>(a.spec, nullptr, nullptr, a.nz, N, a.xp, a.col0, a.col1, a.nz, a.tw, a.inverse, 1.f,
-                                      a.err, st);
+                                      a.err, st, a.nload, a.nstore);
 }
 
 template <int N, int P, int B, int NS>
@@ -229,9 +242,9 @@ cudaError_t launch_z_tma(const ZArgs &a, cudaStream_t st)
     const bool needH = a.mode == ZM_CONV || a.mode == ZM_CORR;
     if (a.mode == ZM_MUL_REAL)
         return launch_col<N, P, B, COL_Z, NS, true>(a.spec, nullptr, a.Hr, N, a.ny, a.xp, a.col0, a.col1, a.ny,
-                                                    a.tw, a.mode, a.scale, a.err, st);
+                                                    a.tw, a.mode, a.scale, a.err, st, a.nload, a.nstore);
     return launch_col<N, P, B, COL_Z, NS>(a.spec, needH ? a.H : nullptr, a.Hr, N, a.ny, a.xp, a.col0, a.col1, a.ny, a.tw,
-                                      a.mode, a.scale, a.err, st);
+                                      a.mode, a.scale, a.err, st, a.nload, a.nstore);
 }
 
 // Y and Z tile widths and stage counts may differ: the Z pass also stages H.
