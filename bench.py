@@ -429,14 +429,38 @@ def run_paper_shape(cr, args):
                "frac": round(v["bytes"] / v["launches"] / (v["ms"] / v["timed"] * 1e-3) / 1e9 / peak, 4)}
            for k, v in sorted(kernels.items(), key=lambda kv: -kv[1]["ms"])}
     value = V * n_iter / (ms * 1e-3) / 1e9
+    flux = abs(out.double().sum().item() / d.double().sum().item() - 1.0)
+    variants = list(cr.cubic_rl_plan_variants(plan)[1])
+    del plan
+
+    # linear (zero-padded, same-mode) boundaries with a 31 x 33 x 33 PSF box, same data
+    kb = (31, 33, 33)
+    c = [k // 2 for k in kb]
+    zz, yy, xx = np.meshgrid(*[np.arange(k) - cc for k, cc in zip(kb, c)], indexing="ij")
+    g = np.exp(-(xx * xx + yy * yy) / (2 * w.psf_sigma_xy ** 2) - zz * zz / (2 * w.psf_sigma_z ** 2))
+    box = torch.from_numpy((g / g.sum()).astype(np.float32)).cuda()
+    lplan = cr.cubic_rl_plan_linear(shape, box)
+    cr.cubic_rl_autotune(lplan, d, out)
+    cr.cubic_rl_deconvolve(lplan, d, n_iter, eps, out)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        cr.cubic_rl_deconvolve(lplan, d, n_iter, eps, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_lin = e0.elapsed_time(e1) / reps
+    linear = {"psf_box": list(kb), "transform_zyx": list(cr.cubic_rl_plan_dims(lplan)[1]),
+              "value": round(V * n_iter / (ms_lin * 1e-3) / 1e9, 3), "unit": UNIT, "ms": round(ms_lin, 3),
+              "variants_xyz": list(cr.cubic_rl_plan_variants(lplan)[1])}
     return {"workload": f"{w.name}: ZYX {shape[0]}x{shape[1]}x{shape[2]}, same-size Gaussian PSF "
                         f"(sigma {w.psf_sigma_xy}, {w.psf_sigma_z}), {n_iter} iterations, Poisson data generated "
                         "on the device",
             "value": round(value, 3), "unit": UNIT, "ms": round(ms, 3),
             "model_84B_frac": round(value * 84.0 / peak, 4),
-            "variants_xyz": list(cr.cubic_rl_plan_variants(plan)[1]),
-            "flux_rel_err": abs(out.double().sum().item() / d.double().sum().item() - 1.0),
-            "kernels": per}
+            "variants_xyz": variants,
+            "flux_rel_err": flux,
+            "kernels": per,
+            "linear": linear}
 
 
 def run_fwd_bwd(cr, args):

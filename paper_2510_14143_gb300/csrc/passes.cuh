@@ -250,7 +250,6 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
         const unsigned q = (unsigned)r / (unsigned)a.ny_img;
         return (int64_t)q * a.ny_spec + ((unsigned)r - q * (unsigned)a.ny_img);
     };
-    const int64_t srow0 = srow(r0), srow1 = srow(r1);  // before the transforms need the registers
     float2 *lpair = xch + l * x_smem_line<N, P>();
     SmemPadded<x_first_radix<N, P>()> sm{lpair};
     auto sync = [] { __syncthreads(); };
@@ -371,8 +370,20 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             float *kb0 = a.keep_a + r0 * N, *kb1 = a.keep_a + r1 * N;
             float *kr0 = a.keep_b + r0 * N, *kr1 = a.keep_b + r1 * N;
             const bool keep = a.keep_a != nullptr;
-            const bool nll = a.nll_stats != nullptr;
-            CFloat c_nll{0.f, 0.f};
+            if (a.nll_stats) {
+                // the likelihood of b, in a loop of its own so that the ratio loop below
+                // keeps its schedule when it is off
+                CFloat c_nll{0.f, 0.f};
+                static_for<0, E>([&](auto i_) {
+                    constexpr int i = CUBIC_CI(i_);
+                    const int n = t + P * i;
+                    const float c0 = fmaxf(v[i].x, eps), c1 = fmaxf(v[i].y, eps);
+                    if (ok0) c_nll = cf_add(c_nll, c0 - p0[n] * logf(c0));
+                    if (ok1) c_nll = cf_add(c_nll, c1 - p1[n] * logf(c1));
+                });
+                const int slot = (int)((block * ((P * L + 31) / 32) + (threadIdx.x >> 5)) & 63);
+                slot_add<P * L>(a.nll_stats + 2 * slot, c_nll);
+            }
             static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
@@ -384,17 +395,8 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
                     if (ok0) { kb0[n] = v[i].x; kr0[n] = x0; }
                     if (ok1) { kb1[n] = v[i].y; kr1[n] = x1; }
                 }
-                if (nll) {
-                    const float c0 = fmaxf(v[i].x, eps), c1 = fmaxf(v[i].y, eps);
-                    if (ok0) c_nll = cf_add(c_nll, c0 - p0[n] * logf(c0));
-                    if (ok1) c_nll = cf_add(c_nll, c1 - p1[n] * logf(c1));
-                }
                 v[i] = make_float2(x0, x1);
             });
-            if (nll) {
-                const int slot = (int)((block * ((P * L + 31) / 32) + (threadIdx.x >> 5)) & 63);
-                slot_add<P * L>(a.nll_stats + 2 * slot, c_nll);
-            }
         } else if constexpr (MODE == XM_UPDATE || MODE == XM_FINAL) {
             // the update writes to dst when given (out of place), else over u
             float *ob = (MODE == XM_FINAL || a.dst) ? a.dst : a.u;
@@ -483,7 +485,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             sm.at(t + P * i) = v[i];
         });
         sync();
-        float2 *q0 = a.spec_out + srow0 * a.xp, *q1 = a.spec_out + srow1 * a.xp;
+        float2 *q0 = a.spec_out + srow(r0) * a.xp, *q1 = a.spec_out + srow(r1) * a.xp;
         static_for<0, E>([&](auto i_) {
             constexpr int i = CUBIC_CI(i_);
             const int k = t + P * i;
