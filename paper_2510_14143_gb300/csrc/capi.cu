@@ -1377,30 +1377,6 @@ __global__ void k_add_mean_grad(float *__restrict__ dbar, const float *__restric
         dbar[i] += add;
 }
 
-// Half-spectrum pointwise kernels over [rows][xp] (columns < xh):
-//   mode 0: s *= H        mode 1: s *= conj(H)
-__global__ void k_spec_mul(float2 *__restrict__ s, const float2 *__restrict__ H, int64_t rows, int64_t xh,
-                           int64_t xp, int mode)
-{
-    const int64_t n = rows * xh;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t o = (i / xh) * xp + i % xh;
-        s[o] = mode ? cmulconj(s[o], H[o]) : cmul(s[o], H[o]);
-    }
-}
-
-//   mode 0: G += conj(A) B     mode 1: G += A conj(B)
-__global__ void k_spec_acc(float2 *__restrict__ G, const float2 *__restrict__ A, const float2 *__restrict__ B,
-                           int64_t rows, int64_t xh, int64_t xp, int mode)
-{
-    const int64_t n = rows * xh;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t o = (i / xh) * xp + i % xh;
-        const float2 p = mode ? cmulconj(A[o], B[o]) : cmulconj(B[o], A[o]);
-        G[o] = cadd(G[o], p);
-    }
-}
-
 // p(x) = h0(x - floor(n/2)) (+= p when accumulate): PSF gradient back to centred indexing
 __global__ void k_origin_to_center(const float *__restrict__ h0, float *__restrict__ p, int64_t nz, int64_t ny,
                                    int64_t nx, int accumulate)
@@ -1430,9 +1406,42 @@ static cubic_status_t enqueue_inverse3(cubic_rl_plan_s *p, float2 *spec, float *
 }
 
 // Recompute iterations k0 .. k0+cnt-1 from u_k0 = seg_u[0], keeping u, b, r, q per iteration.
+// The plain (non-TMA) Z launch shape of the plan's z length: the reverse sweep's extras
+// (saved spectra, PSF-gradient accumulation) exist only there.
+// The widest plain variant (most threads per CTA) is taken.
+static cudaError_t run_z_plain(cubic_rl_plan_s *p, const ZArgs &a, cudaStream_t st)
+{
+    static const int kind[5] = {KK_Z_FWD, KK_Z_CONV, KK_Z_CORR, KK_Z_INV, KK_Z_CONV};
+    int best = -1;
+    for (int v = 0; v < p->kz->nyz; ++v) {
+        const YZVariant &y = p->kz->yzv[v];
+        if (!y.tma && (best < 0 || y.P * y.B > p->kz->yzv[best].P * p->kz->yzv[best].B)) best = v;
+    }
+    if (best < 0) return cudaErrorNotSupported;
+    return counted(p, kind[a.mode], st, [&] { return p->kz->yzv[best].z(a, st); });
+}
+
+// Y forward, the plain Z product (saving its z-transformed input to `save`, and adding
+// conj(V) other or V conj(other) into `gacc`), Y inverse
+static cubic_status_t enqueue_yzy_grad(cubic_rl_plan_s *p, float2 *spec, int zmode, float2 *save, float2 *gacc,
+                                       const float2 *other, int gconj, cudaStream_t st)
+{
+    CUBIC_CUDA(run_y(p, y_args(p, spec, 0, 0, p->xh), st));
+    ZArgs za = z_args(p, spec, zmode, 1.f, 0, p->xh);
+    za.save = save;
+    za.gacc = gacc;
+    za.gother = other;
+    za.gconj = gconj;
+    CUBIC_CUDA(run_z_plain(p, za, st));
+    CUBIC_CUDA(run_y(p, y_args(p, spec, 1, 0, p->xh), st));
+    return CUBIC_OK;
+}
+
+// Recomputes cnt iterations from seg_u[0], keeping u, b, r, q of each and, when seg_U /
+// seg_R are given, the spectra U = DFT(u) and R = DFT(r) that the convolutions form anyway.
 static cubic_status_t enqueue_segment(cubic_rl_plan_s *p, const float *image, float eps, int cnt, float *const *seg_u,
                                       float *const *seg_b, float *const *seg_r, float *const *seg_q, float2 *spec,
-                                      cudaStream_t st)
+                                      cudaStream_t st, float2 *const *seg_U = nullptr, float2 *const *seg_R = nullptr)
 {
     XArgs xa = x_args(p);
     xa.spec_in = spec;
@@ -1443,11 +1452,15 @@ static cubic_status_t enqueue_segment(cubic_rl_plan_s *p, const float *image, fl
     CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
     cubic_status_t s;
     for (int j = 0; j < cnt; ++j) {
-        if ((s = enqueue_yzy(p, spec, ZM_CONV, st)) != CUBIC_OK) return s;
+        s = seg_U ? enqueue_yzy_grad(p, spec, ZM_CONV, seg_U[j], nullptr, nullptr, 0, st)
+                  : enqueue_yzy(p, spec, ZM_CONV, st);
+        if (s != CUBIC_OK) return s;
         xa.keep_a = seg_b[j];
         xa.keep_b = seg_r[j];
         CUBIC_CUDA(run_x(p, XM_RATIO, xa, st));
-        if ((s = enqueue_yzy(p, spec, ZM_CORR, st)) != CUBIC_OK) return s;
+        s = seg_R ? enqueue_yzy_grad(p, spec, ZM_CORR, seg_R[j], nullptr, nullptr, 0, st)
+                  : enqueue_yzy(p, spec, ZM_CORR, st);
+        if (s != CUBIC_OK) return s;
         xa.keep_a = seg_q[j];
         xa.keep_b = nullptr;
         xa.u = seg_u[j];
@@ -1502,7 +1515,8 @@ extern "C" cubic_status_t cubic_rl_backward_workspace_bytes(cubic_rl_plan_t plan
     const size_t vb = ((size_t)plan->V * sizeof(float) + 255) / 256 * 256;
     const size_t sb = (spec_elems(plan) * sizeof(float2) + 255) / 256 * 256;
     const size_t rb = ((kReduceBlocks + 1) * sizeof(double) + 255) / 256 * 256;
-    *bytes = vb * (4 * (size_t)ckpt_every + 1 + 4) + 3 * sb + rb;
+    // u (c + 1), b, r, q (c each), g, ubar, tmp, dbar; spectra U, R (c each) and G
+    *bytes = vb * (4 * (size_t)ckpt_every + 1 + 4) + (2 * (size_t)ckpt_every + 1) * sb + rb;
     return CUBIC_OK;
 }
 
@@ -1549,14 +1563,16 @@ extern "C" cubic_status_t cubic_rl_backward(cubic_rl_plan_t plan, const float *i
     float *ubar = (float *)(m + vb * (4 * c + 2));
     float *tmp = (float *)(m + vb * (4 * c + 3));   // qbar, then rbar / bbar
     float *dbar = (float *)(m + vb * (4 * c + 4));
-    float2 *S1 = (float2 *)(m + vb * (4 * c + 5));
-    float2 *S2 = (float2 *)((unsigned char *)S1 + sb);
-    float2 *G = (float2 *)((unsigned char *)S2 + sb);
+    std::vector<float2 *> seg_U(c), seg_R(c);
+    unsigned char *specs = m + vb * (4 * c + 5);
+    for (int j = 0; j < c; ++j) {
+        seg_U[j] = (float2 *)(specs + sb * j);
+        seg_R[j] = (float2 *)(specs + sb * (c + j));
+    }
+    float2 *G = (float2 *)(specs + sb * 2 * c);
     double *red = (double *)((unsigned char *)G + sb);  // kReduceBlocks + 1 doubles
     float2 *spec = p->ws;
     const unsigned gr = grid_for(V, 256);
-    const int64_t rows = p->rows;
-    const unsigned gs = grid_for(rows * p->xh, 256);
 
     CUBIC_CUDA(cudaMemcpyAsync(g, grad_out, (size_t)V * sizeof(float), cudaMemcpyDeviceToDevice, st));
     CUBIC_CUDA(cudaMemsetAsync(dbar, 0, (size_t)V * sizeof(float), st));
@@ -1568,25 +1584,26 @@ extern "C" cubic_status_t cubic_rl_backward(cubic_rl_plan_t plan, const float *i
         CUBIC_CUDA(cudaMemcpyAsync(seg_u[0], ckpts + (size_t)sg * V, (size_t)V * sizeof(float),
                                    cudaMemcpyDeviceToDevice, st));
         if ((s = enqueue_segment(p, image, eps, cnt, seg_u.data(), seg_b.data(), seg_r.data(), seg_q.data(), spec,
-                                 st)) != CUBIC_OK)
+                                 st, seg_U.data(), seg_R.data())) != CUBIC_OK)
             return s;
+        XArgs xa = x_args(p);
+        xa.spec_in = spec;
+        xa.spec_out = spec;
+        xa.src = tmp;
+        xa.dst = tmp;
         for (int j = cnt - 1; j >= 0; --j) {
             // qbar = g u, ubar = g q
             k_adj_q<<<gr, 256, 0, st>>>(g, seg_u[j], seg_q[j], tmp, ubar, V);
-            // Qbar, R -> G += conj(Qbar) R;  rbar = h * qbar
-            if ((s = enqueue_forward3(p, tmp, S1, 1.f, st)) != CUBIC_OK) return s;
-            if ((s = enqueue_forward3(p, seg_r[j], S2, 1.f, st)) != CUBIC_OK) return s;
-            k_spec_acc<<<gs, 256, 0, st>>>(G, S1, S2, rows, p->xh, p->xp, 0);
-            k_spec_mul<<<gs, 256, 0, st>>>(S1, p->H, rows, p->xh, p->xp, 0);
-            if ((s = enqueue_inverse3(p, S1, tmp, 1.f, st)) != CUBIC_OK) return s;
+            // rbar = h * qbar, with G += conj(Qbar) R in its z pass
+            CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
+            if ((s = enqueue_yzy_grad(p, spec, ZM_CONV, nullptr, G, seg_R[j], 1, st)) != CUBIC_OK) return s;
+            CUBIC_CUDA(run_x(p, XM_INV, xa, st));
             // dbar += rbar / c; bbar
             k_adj_r<<<gr, 256, 0, st>>>(seg_b[j], image, tmp, dbar, eps, V);
-            // Bbar, U -> G += Bbar conj(U);  ubar += h (x) bbar
-            if ((s = enqueue_forward3(p, tmp, S1, 1.f, st)) != CUBIC_OK) return s;
-            if ((s = enqueue_forward3(p, seg_u[j], S2, 1.f, st)) != CUBIC_OK) return s;
-            k_spec_acc<<<gs, 256, 0, st>>>(G, S1, S2, rows, p->xh, p->xp, 1);
-            k_spec_mul<<<gs, 256, 0, st>>>(S1, p->H, rows, p->xh, p->xp, 1);
-            if ((s = enqueue_inverse3(p, S1, tmp, 1.f, st)) != CUBIC_OK) return s;
+            // ubar += h (x) bbar, with G += Bbar conj(U) in its z pass
+            CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
+            if ((s = enqueue_yzy_grad(p, spec, ZM_CORR, nullptr, G, seg_U[j], 0, st)) != CUBIC_OK) return s;
+            CUBIC_CUDA(run_x(p, XM_INV, xa, st));
             k_add<<<gr, 256, 0, st>>>(ubar, tmp, V);
             std::swap(g, ubar);  // g = dL/du_k
         }

@@ -113,6 +113,14 @@ struct ZArgs {
     // linear-boundary plans: planes of the spectrum array that are loaded (the rest of each
     // line reads as zero) and stored; H keeps all N planes.  0: all N
     int64_t nload, nstore;
+    // optional, the product modes of the plain Z kernel (the reverse sweep of the
+    // differentiable path): save receives the z-transformed lines before the product with H;
+    // gacc accumulates conj(V) gother (gconj != 0) or V conj(gother) (gconj = 0), V the
+    // z-transformed lines, all in the spectrum array's layout
+    float2 *save;
+    float2 *gacc;
+    const float2 *gother;
+    int gconj;
 };
 
 // ------------------------------------------------------------------ X pass
@@ -642,6 +650,20 @@ __device__ __forceinline__ void z_body(const ZArgs &a, const int64_t bx, const i
         return;
     }
     const bool corr = a.mode == ZM_CORR;
+    if (ok && a.save) {
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            a.save[off + (int64_t)(t + P * i) * zstride] = v[i];
+        });
+    }
+    if (ok && a.gacc) {
+        static_for<0, E>([&](auto i_) {
+            constexpr int i = CUBIC_CI(i_);
+            const int64_t j = off + (int64_t)(t + P * i) * zstride;
+            const float2 o = __ldg(a.gother + j);
+            a.gacc[j] = cadd(a.gacc[j], a.gconj ? cmulconj(o, v[i]) : cmulconj(v[i], o));
+        });
+    }
     if (a.mode == ZM_MUL_REAL) {
         const float *hb = a.Hr + off;
         static_for<0, E>([&](auto i_) {

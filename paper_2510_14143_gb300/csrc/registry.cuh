@@ -442,6 +442,15 @@ AxisKernels make_axis()
         }
     }
     push_yz(k, make_yzvariant<N, P0, B0>());
+    // Short lines (one to four threads each): a plain variant with more threads per line
+    // (at most 8 elements each) and wide tiles, so that a small volume still fills the GPU
+    // (the reverse sweep's product passes run on the widest plain variant)
+    constexpr int PS = choose_threads(N, 8) > 0 ? choose_threads(N, 8) : P0;
+    constexpr int BS = PS * 64 <= 512 ? 64 : PS * 32 <= 512 ? 32 : 16;
+    if constexpr (P0 <= 4 && N >= 8 && PS * BS <= 512 &&
+                  BS * N * sizeof(float2) + tw_table_size(N, N / PS) * sizeof(float2) <= 220 * 1024) {
+        push_yz(k, make_yzvariant<N, PS, BS>());
+    }
     if constexpr (!S::kTuned && N >= 8 && BY > 0 && P0 * 64 <= 1024 && tma_tile_fits<N, P0, 64, COL_Z>()) {
         // short lines have one or two threads each: a TMA variant whose Z tile is 64
         // columns wide gives the CTA enough threads (thin stacks, e.g. 30 slices)
