@@ -113,6 +113,34 @@ def test_autograd_function_end_to_end(cr):
     assert abs(got[2]) <= 1e-3 * np.abs(gth[:2]).max()       # RL is invariant to the PSF amplitude
 
 
+def test_autograd_batch_over_streams(cr):
+    # five volumes over four streams (one stream carries two): per-volume image gradients
+    # and the PSF-parameter gradient summed over the batch, against the oracle
+    from paper_2510_14143_gb300.autograd import RLDeconvolve
+    shape, nb = (8, 12, 10), 5
+    vols = [synth.make_volume(shape, 2, (1.2, 2.0), 10.0, 1.2, 2.0, 900 + b) for b in range(nb)]
+    d = np.stack([v[0] for v in vols])
+    xt = np.stack([v[1] for v in vols])
+    theta = (1.3, 2.1, 1.0)
+    n_iter, ckpt = 6, 2
+    dt = dev(d).requires_grad_(True)
+    params = [torch.tensor(v, device="cuda", requires_grad=True) for v in theta]
+    u = RLDeconvolve.apply(dt, params[0], params[1], params[2], n_iter, 1e-6, ckpt)
+    loss = ((u - dev(xt)) ** 2).mean(dim=(1, 2, 3)).sum()
+    loss.backward()
+    psf = oracle.psf_gaussian(shape, *theta)
+    rp_sum = np.zeros(shape)
+    for b in range(nb):
+        uo = oracle.rl(d[b], psf, n_iter, 1e-6)
+        assert rel_l2(u[b].detach().cpu().numpy(), uo) <= 1e-4
+        rd, rp = oracle.rl_grad(d[b], psf, n_iter, 1e-6, 2 * (uo - xt[b]) / uo.size)
+        assert rel_l2(dt.grad[b].cpu().numpy(), rd) <= 1e-3
+        rp_sum += rp
+    gth = oracle.psf_gaussian_grad(shape, *theta, rp_sum)
+    got = np.array([p.grad.item() for p in params])
+    assert np.allclose(got[:2], gth[:2], rtol=1e-3)
+
+
 def test_differentiable_workload_sample(cr):
     # one volume of the 16 x 128x128x64 workload, 30 iterations, checkpoints every 6
     d, xt = synth.grad_volume(0)
