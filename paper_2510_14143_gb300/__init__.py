@@ -376,6 +376,28 @@ def n_checkpoints(n_iter: int, ckpt_every: int) -> int:
     return (int(n_iter) + int(ckpt_every) - 1) // int(ckpt_every)
 
 
+def shard_volumes(shapes, world: int):
+    """Volume indices for each of `world` GPUs, balanced by voxel count.
+
+    A batch of independent volumes needs no exchange between GPUs: each one deconvolves its
+    share.  Greedy longest-processing-time order: the largest remaining volume goes to the
+    least-loaded GPU (the lower index on ties), so every rank computes the same split on
+    its own.  Returns `world` lists of indices, each in increasing order.
+    """
+    world = int(world)
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    vox = [int(s[0]) * int(s[1]) * int(s[2]) for s in shapes]
+    order = sorted(range(len(vox)), key=lambda i: (-vox[i], i))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += vox[i]
+    return [sorted(p) for p in parts]
+
+
 def cubic_rl_deconvolve_ckpt(plan: Plan, image, n_iter: int, eps: float, ckpt_every: int, ckpts, out,
                              stream=None) -> None:
     import torch

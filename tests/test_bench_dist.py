@@ -1,8 +1,9 @@
 """The benchmark's multi-rank logic on CPU: two gloo ranks, no GPU.
 
-A single volume does not shard, so N ranks run independent replicas; the only
-collectives are a barrier and the max of the elapsed time, and the whole-job
-rate counts every rank's units over the slowest rank's time.
+A single volume does not shard, so N ranks run independent replicas of it; a
+batch of volumes is split across the ranks by voxel count.  The only collectives
+are a barrier and the max of the elapsed time, and the whole-job rate counts
+every rank's units over the slowest rank's time.
 """
 import json
 import os
@@ -70,3 +71,54 @@ def test_reference_arm_prints_once_under_two_ranks():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_shard_volumes_balanced_and_complete():
+    sys.path.insert(0, ROOT)
+    import paper_2510_14143_gb300 as cr
+    from paper_2510_14143_gb300 import synth
+    shapes = synth.batch_shapes()
+    vox = [a * b * c for a, b, c in shapes]
+    for world in (1, 2, 3, 4, 8):
+        parts = cr.shard_volumes(shapes, world)
+        assert len(parts) == world
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(shapes)))             # every volume exactly once
+        loads = [sum(vox[i] for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(vox)          # greedy balance bound
+        assert parts == cr.shard_volumes(shapes, world)     # every rank computes the same split
+    with pytest.raises(ValueError):
+        cr.shard_volumes(shapes, 0)
+
+
+def _shard_worker(rank, world, port, q):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                      MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_2510_14143_gb300 as cr
+    from paper_2510_14143_gb300 import synth
+    r = bench.Ranks("gloo")
+    shapes = synth.batch_shapes()
+    mine = cr.shard_volumes(shapes, r.world)[r.rank]
+    load = float(sum(a * b * c for a, b, c in (shapes[i] for i in mine)))
+    q.put((rank, mine, load, r.max(load)))
+    r.barrier()
+    r.close()
+
+
+def test_two_gloo_ranks_split_the_batch():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, a, la, ma), (_, b, lb, mb) = out
+    assert not set(a) & set(b) and len(a) + len(b) == 64    # disjoint, whole batch
+    assert ma == mb == max(la, lb)                          # both ranks see the slowest share

@@ -1,0 +1,66 @@
+"""The 1024x1024x128 workload in the launch configuration the benchmark times (autotuned
+shapes, Gaussian PSF with a real spectrum).
+
+Two iterations are compared with the FP64 oracle over the whole volume.  The benchmarked
+50 iterations are checked through properties that hold at any size: flux conservation
+(every RL step keeps sum(u) = sum(d) for a normalised PSF while the clamp is inactive)
+and nonnegativity.  The host-buffer entry point must give the device path's result bitwise.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_14143_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cr():
+    from paper_2510_14143_gb300 import build
+    build.build()
+    import paper_2510_14143_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def large(cr):
+    w = synth.LARGE
+    d, _ = synth.workload_volume(w)
+    psf = torch.empty(w.shape, dtype=torch.float32, device="cuda")
+    cr.cubic_psf_gaussian(w.shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0, psf)
+    plan = cr.cubic_rl_plan(w.shape, psf)
+    dd = torch.from_numpy(d).cuda()
+    out = torch.empty_like(dd)
+    cr.cubic_rl_autotune(plan, dd, out)
+    return w, d, dd, psf, plan
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def test_large_two_iterations_match_oracle(cr, large):
+    w, d, dd, psf, plan = large
+    out = torch.empty_like(dd)
+    cr.cubic_rl_deconvolve(plan, dd, 2, 1e-6, out)
+    torch.cuda.synchronize()
+    ref = oracle.rl(d, psf.cpu().numpy(), 2, 1e-6)
+    err = rel_l2(out.cpu().numpy(), ref)
+    print(f"rl 1024x1024x128, 2 it, tuned shapes {cr.cubic_rl_plan_variants(plan)[1]}: rel-L2 = {err:.3e}")
+    assert err <= 1e-5
+
+
+def test_large_benchmarked_run_properties(cr, large):
+    w, d, dd, psf, plan = large
+    out = torch.empty_like(dd)
+    cr.cubic_rl_deconvolve(plan, dd, w.n_iter, 1e-6, out)
+    cr.cubic_rl_stream_status(plan)
+    flux = dd.double().sum().item()
+    assert abs(out.double().sum().item() - flux) <= 1e-5 * flux
+    assert out.min().item() >= 0.0
+    h_in = torch.from_numpy(d).pin_memory()
+    h_out = torch.empty(w.shape, dtype=torch.float32).pin_memory()
+    cr.cubic_rl_deconvolve_host(plan, h_in, w.n_iter, 1e-6, h_out)
+    assert torch.equal(h_out, out.cpu())
