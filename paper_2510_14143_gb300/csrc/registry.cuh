@@ -417,6 +417,14 @@ AxisKernels make_axis()
     k.xm[XM_FINAL] = launch_x_multi<N, P0, XL, XM_FINAL>;
     k.xm_lines = XL;
     constexpr int B0 = plain_cols<N, P0>();
+    // Short lines (one to four threads each): the plain shape with more threads per line
+    // (at most 8 elements each) and wide tiles, so that small volumes still fill the GPU
+    constexpr int PS = choose_threads(N, 8) > 0 ? choose_threads(N, 8) : P0;
+    constexpr int BS = PS * 64 <= 512 ? 64 : PS * 32 <= 512 ? 32 : 16;
+    constexpr bool kWide = P0 <= 4 && N >= 8 && PS * BS <= 512 &&
+                           BS * N * sizeof(float2) + tw_table_size(N, N / PS) * sizeof(float2) <= 220 * 1024;
+    // the batched path's multi-volume launches keep the default shape: the wide one
+    // measured slower there (129.7 against 122.9 ms for the 64-volume batch)
     k.ym = launch_y_multi<N, P0, B0>;
     k.zm = launch_z_multi<N, P0, B0>;
     k.m_cols = B0;
@@ -442,15 +450,9 @@ AxisKernels make_axis()
         }
     }
     push_yz(k, make_yzvariant<N, P0, B0>());
-    // Short lines (one to four threads each): a plain variant with more threads per line
-    // (at most 8 elements each) and wide tiles, so that a small volume still fills the GPU
-    // (the reverse sweep's product passes run on the widest plain variant)
-    constexpr int PS = choose_threads(N, 8) > 0 ? choose_threads(N, 8) : P0;
-    constexpr int BS = PS * 64 <= 512 ? 64 : PS * 32 <= 512 ? 32 : 16;
-    if constexpr (P0 <= 4 && N >= 8 && PS * BS <= 512 &&
-                  BS * N * sizeof(float2) + tw_table_size(N, N / PS) * sizeof(float2) <= 220 * 1024) {
-        push_yz(k, make_yzvariant<N, PS, BS>());
-    }
+    // the wide plain shape as a tuning choice too (the reverse sweep's product passes run
+    // on the widest plain variant)
+    if constexpr (kWide) push_yz(k, make_yzvariant<N, PS, BS>());
     if constexpr (!S::kTuned && N >= 8 && BY > 0 && P0 * 64 <= 1024 && tma_tile_fits<N, P0, 64, COL_Z>()) {
         // short lines have one or two threads each: a TMA variant whose Z tile is 64
         // columns wide gives the CTA enough threads (thin stacks, e.g. 30 slices)
