@@ -75,6 +75,7 @@ def _load():
                 "orc_poisson_nll": ([P, P, i64, cd], cd),
                 "orc_conv_same": ([P, P, P, i64, i64, i64, i64, i64, i64, ci], ci),
                 "orc_rl_same": ([P, P, i64, i64, i64, i64, i64, i64, ci, cd, P], ci),
+                "orc_rl_accel_same": ([P, P, i64, i64, i64, i64, i64, i64, ci, cd, P, P], ci),
                 "orc_psnr_si": ([P, P, i64], cd),
                 "orc_rl_monitor": ([P, P, P, i64, i64, i64, ci, cd, ci, cd, ci, P, ctypes.POINTER(ci), P], ci),
                 "orc_accel_linear": ([i64, ci, P, P, P, P, P], ci),
@@ -216,6 +217,16 @@ def rl_same(d, psf, n_iter: int, eps: float = 1e-6) -> np.ndarray:
     out = np.empty_like(dd)
     _check(_load().orc_rl_same(_p(dd), _p(p), *dd.shape, *p.shape, int(n_iter), float(eps), _p(out)), "rl_same")
     return out
+
+
+def rl_accel_same(d, psf, n_iter: int, eps: float = 1e-6):
+    """Accelerated RL with linear boundaries; returns (estimate, alpha_0..alpha_{n-1})."""
+    dd, p = _f64(d), _f64(psf)
+    out = np.empty_like(dd)
+    alpha = np.zeros(max(1, int(n_iter)), np.float64)
+    _check(_load().orc_rl_accel_same(_p(dd), _p(p), *dd.shape, *p.shape, int(n_iter), float(eps), _p(out),
+                                     _p(alpha)), "rl_accel_same")
+    return out, alpha[:int(n_iter)].copy()
 
 
 def poisson_nll(b, d, eps: float) -> float:

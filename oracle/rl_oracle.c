@@ -743,6 +743,54 @@ int orc_accel_linear(int64_t V, int n_iter, const double *xs, const double *lamb
     return accel_run(lin_step, &c, V, n_iter, x0, out, alpha_hist);
 }
 
+/* Accelerated RL with linear boundaries: the same extrapolation, each step a same-mode
+ * RL iteration. */
+struct same_step_ctx {
+    const struct same_geom *g;
+    const cplx *H;
+    cplx *work;
+    const double *d;
+    double eps;
+    double *b, *q;
+};
+
+static int same_rl_step(void *ctx, const double *y, double *x_next)
+{
+    const struct same_step_ctx *c = ctx;
+    const int64_t V = c->g->nz * c->g->ny * c->g->nx;
+    int rc = same_filter(c->g, c->H, y, c->b, c->work, 0);
+    if (rc) return rc;
+    for (int64_t i = 0; i < V; ++i) c->b[i] = c->d[i] / (c->b[i] > c->eps ? c->b[i] : c->eps);
+    rc = same_filter(c->g, c->H, c->b, c->q, c->work, 1);
+    if (rc) return rc;
+    for (int64_t i = 0; i < V; ++i) x_next[i] = y[i] * c->q[i];
+    return 0;
+}
+
+int orc_rl_accel_same(const double *d, const double *psf, int64_t nz, int64_t ny, int64_t nx, int64_t kz, int64_t ky,
+                      int64_t kx, int n_iter, double eps, double *out, double *alpha_hist)
+{
+    if (!d || !psf || !out || nz < 1 || ny < 1 || nx < 1 || kz < 1 || ky < 1 || kx < 1 || n_iter < 0 ||
+        !(eps > 0))
+        return -1;
+    const int64_t n[3] = {nz, ny, nx}, k[3] = {kz, ky, kx};
+    int64_t V = nz * ny * nx;
+    struct same_geom g;
+    cplx *H, *work;
+    int rc = same_setup(psf, n, k, &g, &H, &work);
+    double *x0 = malloc(sizeof(double) * (size_t)V), *b = malloc(sizeof(double) * (size_t)V);
+    double *q = malloc(sizeof(double) * (size_t)V);
+    if (!x0 || !b || !q) rc = rc ? rc : -2;
+    if (!rc) {
+        double u0 = orc_initial_value(d, V, eps);
+        for (int64_t i = 0; i < V; ++i) x0[i] = u0;
+        struct same_step_ctx c = {&g, H, work, d, eps, b, q};
+        rc = accel_run(same_rl_step, &c, V, n_iter, x0, out, alpha_hist);
+    }
+    free(H); free(work); free(x0); free(b); free(q);
+    return rc;
+}
+
 /* Fourier Shell Correlation of two volumes (the paper's FRC/FSC resolution metric,
  * Section 3 "custom algorithms" and Section 4 "Evaluation metrics"):
  *   FSC(s) = Re sum_{k in s} A(k) conj B(k) / sqrt(sum_{k in s} |A(k)|^2 sum_{k in s} |B(k)|^2),

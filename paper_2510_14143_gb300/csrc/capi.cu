@@ -838,15 +838,15 @@ static cubic_status_t lin_crop(cubic_rl_plan_s *p, const float *padded, float *o
 
 static cubic_status_t enqueue_yzy(cubic_rl_plan_s *p, float2 *spec, int zmode, cudaStream_t st);
 
-// RL of a linear plan: the image and the estimate live in the plan's padded arrays
-static cubic_status_t enqueue_rl_linear(cubic_rl_plan_s *p, const float *image, int n_iter, float eps, float *out,
-                                       float2 *spec, cudaStream_t st)
+// A linear plan's start: the image padded into dp, and the estimate x_0 = max(mean, eps)
+// on its box (zero padding elsewhere) in up; the mean is over the image's voxels, to which
+// the padding adds nothing.
+static cubic_status_t lin_init(cubic_rl_plan_s *p, const float *image, float eps, float *dp, float *up,
+                               cudaStream_t st)
 {
-    float *dp = p->lin, *up = p->lin + lin_elems(p);
     const int64_t R = p->iz * p->iy, E = (int64_t)lin_elems(p);
     cubic_status_t s = lin_pad(p, image, dp, st);
     if (s != CUBIC_OK) return s;
-    // the mean over the image's voxels: the zero padding adds nothing to the sum
     CUBIC_CUDA(counted(p, KK_SUM, st, [&] {
         k_sum_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(dp, E, p->partial);
         k_sum_final<<<1, kReduceThreads, 0, st>>>(p->partial, kReduceBlocks, p->partial + kReduceBlocks);
@@ -856,6 +856,16 @@ static cubic_status_t enqueue_rl_linear(cubic_rl_plan_s *p, const float *image, 
         k_fill_padded<<<grid_for(E, 256), 256, 0, st>>>(up, R, p->ix, p->nx, p->partial + kReduceBlocks, p->V, eps);
         return cudaGetLastError();
     }));
+    return CUBIC_OK;
+}
+
+// RL of a linear plan: the image and the estimate live in the plan's padded arrays
+static cubic_status_t enqueue_rl_linear(cubic_rl_plan_s *p, const float *image, int n_iter, float eps, float *out,
+                                       float2 *spec, cudaStream_t st)
+{
+    float *dp = p->lin, *up = p->lin + lin_elems(p);
+    cubic_status_t s = lin_init(p, image, eps, dp, up, st);
+    if (s != CUBIC_OK) return s;
     if (n_iter > 0) {
         XArgs xa = x_args(p);
         xa.spec_in = spec;
@@ -1773,7 +1783,6 @@ extern "C" cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const f
                                                    double *history, void *stream)
 {
     if (!plan || !image || !out || !n_done) return fail(CUBIC_ERR_INVALID_ARG, "plan, image, out, n_done must be non-null");
-    if (cubic_status_t g = no_linear(plan, "automatic stopping")) return g;
     if (max_iter < 1 || check_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "max_iter and check_every must be >= 1");
     if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
     if (!(tol >= 0.f) || !(tol < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "tol must be finite and >= 0");
@@ -1798,14 +1807,18 @@ extern "C" cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const f
     }
     cudaStream_t st = (cudaStream_t)stream;
     CUBIC_CUDA(cudaMemsetAsync(p->auto_stats, 0, (size_t)max_iter * 256 * sizeof(float), st));
-    if ((s = enqueue_init(p, image, eps, out, st)) != CUBIC_OK) return s;
+    // a linear plan iterates on its padded arrays (the padding contributes zeros to the sums)
+    float *uw = p->linear ? p->lin + lin_elems(p) : out;
+    const float *dw = p->linear ? p->lin : image;
+    s = p->linear ? lin_init(p, image, eps, p->lin, uw, st) : enqueue_init(p, image, eps, out, st);
+    if (s != CUBIC_OK) return s;
     XArgs xa = x_args(p);
     xa.spec_in = p->ws;
     xa.spec_out = p->ws;
-    xa.src = out;
-    xa.u = out;
-    xa.dst = out;
-    xa.d = image;
+    xa.src = uw;
+    xa.u = uw;
+    xa.dst = uw;
+    xa.d = dw;
     xa.eps = eps;
     CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
     int k = 0;
@@ -1823,9 +1836,10 @@ extern "C" cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const f
             float delta = 0.f;
             CUBIC_CUDA(cudaMemcpyAsync(&delta, p->auto_delta + k - 1, sizeof(float), cudaMemcpyDeviceToHost, st));
             CUBIC_CUDA(cudaStreamSynchronize(st));
-            if (delta < tol) break;  // out already holds u_k (the update wrote it)
+            if (delta < tol) break;  // the estimate already holds u_k (the update wrote it)
         }
     }
+    if (p->linear && (s = lin_crop(p, uw, out, st)) != CUBIC_OK) return s;
     *n_done = k;
     if (history) {
         std::vector<float> h((size_t)k);
@@ -1894,10 +1908,16 @@ __global__ void __launch_bounds__(1024) k_acc_alpha(const float4 *__restrict__ p
     }
 }
 
+// the padded arrays' size for a linear plan
+static size_t acc_vol_bytes(const cubic_rl_plan_s *p)
+{
+    return ((p->linear ? lin_elems(p) : (size_t)p->V) * sizeof(float) + 255) / 256 * 256;
+}
+
 static cubic_status_t ensure_accel(cubic_rl_plan_s *p)
 {
     if (p->acc) return CUBIC_OK;
-    const size_t vol = ((size_t)p->V * sizeof(float) + 255) / 256 * 256;
+    const size_t vol = acc_vol_bytes(p);
     const size_t nb = (size_t)((p->rows + 1) / 2);  // most X blocks: one line pair each
     const size_t part = (nb * sizeof(float4) + 255) / 256 * 256;
     void *m = nullptr;
@@ -1915,7 +1935,6 @@ extern "C" cubic_status_t cubic_rl_deconvolve_accel(cubic_rl_plan_t plan, const 
                                                     float *out, float *alpha, void *stream)
 {
     if (!plan || !image || !out) return fail(CUBIC_ERR_INVALID_ARG, "plan, image and out must be non-null");
-    if (cubic_status_t g = no_linear(plan, "accelerated RL")) return g;
     if (n_iter < 0) return fail(CUBIC_ERR_INVALID_ARG, "n_iter must be >= 0");
     if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
     if (!aligned16(image) || !aligned16(out)) return fail(CUBIC_ERR_ALIGNMENT, "image and out must be 16-byte aligned");
@@ -1927,15 +1946,22 @@ extern "C" cubic_status_t cubic_rl_deconvolve_accel(cubic_rl_plan_t plan, const 
     if (s != CUBIC_OK) return s;
     if ((s = ensure_accel(p)) != CUBIC_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t vol = ((size_t)p->V * sizeof(float) + 255) / 256 * 256 / sizeof(float);
+    const size_t vol = acc_vol_bytes(p) / sizeof(float);
     float *xc = p->acc, *xn = p->acc + vol, *y = p->acc + 2 * vol, *gc = p->acc + 3 * vol, *gn = p->acc + 4 * vol;
-
-    if ((s = enqueue_init(p, image, eps, xc, st)) != CUBIC_OK) return s;  // x_0 = max(mean(d), eps)
-    if (n_iter == 0) {
-        CUBIC_CUDA(cudaMemcpyAsync(out, xc, (size_t)p->V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    // a linear plan iterates on zero-padded rows: the padding stays 0 under the update and
+    // the prediction, and adds 0 to the dot products
+    const size_t nw = p->linear ? lin_elems(p) : (size_t)p->V;
+    const float *dw = p->linear ? p->lin : image;
+    auto finish = [&](const float *x) -> cubic_status_t {
+        if (p->linear) return lin_crop(p, x, out, st);
+        CUBIC_CUDA(cudaMemcpyAsync(out, x, nw * sizeof(float), cudaMemcpyDeviceToDevice, st));
         return CUBIC_OK;
-    }
-    CUBIC_CUDA(cudaMemcpyAsync(y, xc, (size_t)p->V * sizeof(float), cudaMemcpyDeviceToDevice, st));  // y_0 = x_0
+    };
+
+    s = p->linear ? lin_init(p, image, eps, p->lin, xc, st) : enqueue_init(p, image, eps, xc, st);  // x_0
+    if (s != CUBIC_OK) return s;
+    if (n_iter == 0) return finish(xc);
+    CUBIC_CUDA(cudaMemcpyAsync(y, xc, nw * sizeof(float), cudaMemcpyDeviceToDevice, st));  // y_0 = x_0
     CUBIC_CUDA(cudaMemsetAsync(p->acc_state, 0, 2 * sizeof(float), st));
     if (alpha) CUBIC_CUDA(cudaMemsetAsync(alpha, 0, (size_t)n_iter * sizeof(float), st));
 
@@ -1945,7 +1971,7 @@ extern "C" cubic_status_t cubic_rl_deconvolve_accel(cubic_rl_plan_t plan, const 
     XArgs xa = x_args(p);
     xa.spec_in = p->ws;
     xa.spec_out = p->ws;
-    xa.d = image;
+    xa.d = dw;
     xa.eps = eps;
     xa.src = y;
     CUBIC_CUDA(run_x(p, XM_FWD, xa, st));  // spectrum of y_0
@@ -1956,12 +1982,12 @@ extern "C" cubic_status_t cubic_rl_deconvolve_accel(cubic_rl_plan_t plan, const 
         const bool last = k + 1 == n_iter;
         XArgs xu = xa;                                                       // x_{k+1} = y_k q, g_k
         xu.u = y;
-        xu.dst = last ? out : xn;
+        xu.dst = (last && !p->linear) ? out : xn;
         xu.acc_g = gn;
         xu.acc_gprev = k >= 1 ? gc : nullptr;
         xu.acc_part = p->acc_part;
         CUBIC_CUDA(run_x_as(p, XM_FINAL, KK_X_ACC_UPDATE, xu, spec + (k >= 1 ? 4 : 3) * real, st));
-        if (last) break;
+        if (last) return p->linear ? lin_crop(p, xn, out, st) : CUBIC_OK;
         CUBIC_CUDA(counted(p, KK_ACC_ALPHA, st, [&] {
             k_acc_alpha<<<1, 1024, 0, st>>>(p->acc_part, nblocks, k, p->acc_state, alpha, n_iter);
             return cudaGetLastError();

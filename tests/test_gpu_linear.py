@@ -121,13 +121,42 @@ def test_linear_autotune_and_update_psf(cr):
     assert rel_l2(out.cpu().numpy(), oracle.rl_same(d, psf, 10, 1e-6)) <= 1e-4
 
 
+@pytest.mark.parametrize("n,k", [((24, 40, 48), (7, 9, 9)), ((9, 15, 30), (5, 5, 3))])
+def test_linear_accelerated_matches_oracle(cr, n, k):
+    d, _ = synth.make_volume(n, 3, (1.5, 3.0), 10.0, 1.5, 3.0, 41 + sum(n))
+    psf = gaussian_box(k, 1.3, 2.2)
+    plan = cr.cubic_rl_plan_linear(n, dev(psf))
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    alpha = torch.empty(12, dtype=torch.float32, device="cuda")
+    cr.cubic_rl_deconvolve_accel(plan, dev(d), 12, 1e-6, out, alpha)
+    torch.cuda.synchronize()
+    ref, a_ref = oracle.rl_accel_same(d, psf, 12, 1e-6)
+    assert rel_l2(out.cpu().numpy(), ref) <= 1e-4
+    assert np.allclose(alpha.cpu().numpy(), a_ref, atol=1e-3)
+
+
+def test_linear_automatic_stopping(cr):
+    n, k = (24, 40, 48), (7, 9, 9)
+    d, _ = synth.make_volume(n, 3, (1.5, 3.0), 10.0, 1.5, 3.0, 57)
+    psf = gaussian_box(k, 1.3, 2.2)
+    plan = cr.cubic_rl_plan_linear(n, dev(psf))
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    n_all, hist = cr.cubic_rl_deconvolve_auto(plan, dev(d), 25, 1e-6, 0.0, 1, out)
+    assert n_all == 25 and all(h2 < h1 for h1, h2 in zip(hist[1:], hist[2:]))
+    tol = 0.5 * (hist[9] + hist[10])
+    n_stop, _ = cr.cubic_rl_deconvolve_auto(plan, dev(d), 25, 1e-6, tol, 1, out)
+    assert n_stop == 11                      # the first check with delta under tol
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), oracle.rl_same(d, psf, n_stop, 1e-6)) <= 1e-4
+
+
 def test_linear_plan_errors(cr):
     n, k = (8, 10, 12), (3, 3, 3)
     plan = cr.cubic_rl_plan_linear(n, dev(np.ones(k, np.float32)))
     img = dev(np.ones(n, np.float32))
     out = torch.empty_like(img)
-    for call in (lambda: cr.cubic_rl_deconvolve_accel(plan, img, 3, 1e-6, out),
-                 lambda: cr.cubic_rl_deconvolve_auto(plan, img, 3, 1e-6, 0.0, 1, out),
+    for call in (lambda: cr.cubic_rl_deconvolve_monitor(plan, img, 3, 1e-6, cr.METRIC_NLL, 0.0, 1, out),
+                 lambda: cr.cubic_rl_deconvolve_ckpt(plan, img, 3, 1e-6, 1, torch.empty((3,) + n, device="cuda"), out),
                  lambda: cr.cubic_fsc(plan, img, out, 4)):
         with pytest.raises(cr.CubicError) as e:
             call()

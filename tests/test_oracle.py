@@ -757,3 +757,18 @@ def test_rl_same_matches_direct_path_and_keeps_flux():
     assert abs(got.sum() - d.sum()) <= 1e-11 * d.sum()
     # a 1-voxel PSF makes the first iterate the image itself
     assert np.allclose(oracle.rl_same(d, np.array([[[0.7]]]), 1, 1e-6), d, rtol=1e-12)
+
+
+def test_rl_accel_same_composition():
+    # the extrapolation (pinned above) around the same-mode step (pinned by direct loops):
+    # the first two iterates are plain same-mode RL, flux stays, alpha stays in [0, 1]
+    r = np.random.default_rng(95)
+    d = r.uniform(1, 20, (5, 6, 7))
+    psf = r.uniform(0.1, 1, (3, 3, 5))
+    psf /= psf.sum()
+    for n in (0, 1, 2):
+        x, a = oracle.rl_accel_same(d, psf, n, 1e-6)
+        assert np.allclose(x, oracle.rl_same(d, psf, n, 1e-6), rtol=1e-13, atol=0) and np.all(a == 0)
+    x, a = oracle.rl_accel_same(d, psf, 10, 1e-6)
+    assert abs(x.sum() - d.sum()) <= 1e-11 * d.sum() and x.min() >= 0
+    assert np.all((a >= 0) & (a <= 1)) and a[2:].max() > 0.3
