@@ -284,6 +284,7 @@ def run_ours(args, w: synth.Workload):
         result["fwd_bwd"] = run_fwd_bwd(cr, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, d_host, args.cpu_sample)
+        result["accuracy"] = accuracy(cr, plan, d, d_host, w)
     ranks.close()
     return rank, result
 
@@ -593,6 +594,35 @@ def cpu_baseline(w: synth.Workload, d_host, sample: str, iters: int = 1):
             "sample": f"{iters} RL iteration(s) of the FP64 oracle on a {dd.shape[2]}x{dd.shape[1]}x{dd.shape[0]} "
                       f"{'volume' if sample == 'full' else 'crop'} of the workload (PSF spectrum precomputed), "
                       f"{dt:.1f} s"}
+
+
+def accuracy(cr, plan, d, d_host, w: synth.Workload):
+    """Relative L2 error of the float32 GPU estimate against the FP64 oracle, per workload:
+    the small one at its 20 iterations (the gated tolerance is 1e-4), 256x256x128 at 10 and
+    the timed volume in its benchmarked launch configuration at 2 (reported, not gated)."""
+    import torch
+    import oracle
+
+    def err(plan_, img, img_host, psf_host, n):
+        out = torch.empty_like(img)
+        cr.cubic_rl_deconvolve(plan_, img, n, 1e-6, out)
+        ref = oracle.rl(img_host, psf_host, n, 1e-6)
+        diff = out.cpu().numpy().astype(np.float64) - ref
+        return float(np.linalg.norm(diff) / np.linalg.norm(ref))
+
+    res = {}
+    for wl, n in ((synth.SMALL, synth.SMALL.n_iter), (synth.MEDIUM, 10)):
+        dh, _ = synth.workload_volume(wl)
+        psf = torch.empty(wl.shape, dtype=torch.float32, device="cuda")
+        cr.cubic_psf_gaussian(wl.shape, wl.psf_sigma_xy, wl.psf_sigma_z, 1.0, psf)
+        p = cr.cubic_rl_plan(wl.shape, psf)
+        res[wl.name] = {"n_iter": n, "rel_l2": err(p, torch.from_numpy(dh).cuda(), dh, psf.cpu().numpy(), n)}
+    psf = torch.empty(w.shape, dtype=torch.float32, device="cuda")
+    cr.cubic_psf_gaussian(w.shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0, psf)
+    res[w.name] = {"n_iter": 2, "rel_l2": err(plan, d, d_host, psf.cpu().numpy(), 2),
+                   "launch_shapes_xyz": list(cr.cubic_rl_plan_variants(plan)[1])}
+    res["reference"] = "FP64 CPU oracle, same inputs and PSF"
+    return res
 
 
 def run_reference(args, w: synth.Workload):
