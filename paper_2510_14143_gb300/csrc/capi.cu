@@ -2342,20 +2342,25 @@ extern "C" cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const 
 
 namespace {
 
+// One multi-volume launch: the volumes whose axis has the same length, launched with
+// launch shape `shape` (an index into k->xv for X, into k->yzv for Y and Z)
 struct XGroup {
     const AxisKernels *k;
     MultiTable<XArgs> *tab;
     int64_t blocks;
+    int shape;
 };
 struct YGroup {
     const AxisKernels *k;
     MultiTable<YArgs> *tab;
     int64_t blocks;
+    int shape;
 };
 struct ZGroup {
     const AxisKernels *k;
     MultiTable<ZArgs> *tab;
     int64_t blocks;
+    int shape;
 };
 
 struct BatchState {
@@ -2393,13 +2398,13 @@ static cubic_status_t enqueue_batched(BatchState &b, cudaStream_t st)
     }
     if (b.n_iter == 0) return CUBIC_OK;
     auto xstage = [&](int mode) -> cubic_status_t {
-        for (const XGroup &g : b.gx) CUBIC_CUDA(g.k->xm[mode](g.tab, g.blocks, st));
+        for (const XGroup &g : b.gx) CUBIC_CUDA(g.k->xv[g.shape].m[mode](g.tab, g.blocks, st));
         return CUBIC_OK;
     };
     auto yzy = [&](int zmode) -> cubic_status_t {
-        for (const YGroup &g : b.gy) CUBIC_CUDA(g.k->ym(g.tab, g.blocks, 0, st));
-        for (const ZGroup &g : b.gz) CUBIC_CUDA(g.k->zm(g.tab, g.blocks, zmode, st));
-        for (const YGroup &g : b.gy) CUBIC_CUDA(g.k->ym(g.tab, g.blocks, 1, st));
+        for (const YGroup &g : b.gy) CUBIC_CUDA(g.k->yzv[g.shape].ym(g.tab, g.blocks, 0, st));
+        for (const ZGroup &g : b.gz) CUBIC_CUDA(g.k->yzv[g.shape].zm(g.tab, g.blocks, zmode, st));
+        for (const YGroup &g : b.gy) CUBIC_CUDA(g.k->yzv[g.shape].ym(g.tab, g.blocks, 1, st));
         return CUBIC_OK;
     };
     cubic_status_t s = xstage(XM_FWD);
@@ -2412,16 +2417,201 @@ static cubic_status_t enqueue_batched(BatchState &b, cudaStream_t st)
     return s;
 }
 
-// Group volumes by axis length and build the device tables.
-static cubic_status_t build_batch(BatchState &b)
+// ---- launch shapes of the batched path
+// For every axis length and pass (X, Y, Z) the shape comes from this table, filled by
+// timing the candidates on the first batch that has the length (batch_tune); until then,
+// and where tuning fails, the default shape serves.
+static std::mutex g_bshape_mu;
+static std::map<std::pair<int64_t, int>, int> g_bshape;  // (length, pass 0/1/2) -> variant index
+
+// the default shapes: X with the multi launcher's line count, Y/Z the P0 x m_cols plain one
+static int default_xshape(const AxisKernels *k)
+{
+    for (int v = 0; v < k->nx; ++v)
+        if (k->xv[v].L == k->xm_lines && k->xv[v].m[XM_FWD]) return v;
+    return 0;
+}
+static int default_yzshape(const AxisKernels *k)
+{
+    int first = -1;
+    for (int v = 0; v < k->nyz; ++v) {
+        if (!k->yzv[v].ym) continue;
+        if (k->yzv[v].B == k->m_cols) return v;  // the first plain variant: P0 x m_cols
+        if (first < 0) first = v;
+    }
+    return first < 0 ? 0 : first;
+}
+
+static int chosen_shape(int64_t len, int pass, int fallback)
+{
+    std::lock_guard<std::mutex> lk(g_bshape_mu);
+    auto it = g_bshape.find({len, pass});
+    return it == g_bshape.end() ? fallback : it->second;
+}
+
+// Host table of one group for one launch shape; returns its block count.
+static int64_t fill_xtable(const BatchState &b, const std::vector<int> &vols, const AxisKernels *k, int shape,
+                    MultiTable<XArgs> *t)
+{
+    t->nvol = (int)vols.size();
+    int64_t blocks = 0;
+    const int L = k->xv[shape].L;
+    for (int i = 0; i < t->nvol; ++i) {
+        cubic_rl_plan_s *p = b.plans[vols[i]];
+        XArgs a = x_args(p);
+        a.spec_in = p->ws;
+        a.spec_out = p->ws;
+        a.src = b.outs[vols[i]];
+        a.u = b.outs[vols[i]];
+        a.dst = b.outs[vols[i]];
+        a.d = b.images[vols[i]];
+        a.eps = b.eps;
+        t->args[i] = a;
+        t->prefix[i] = blocks;
+        blocks += ((p->rows + 1) / 2 + L - 1) / L;
+    }
+    t->prefix[t->nvol] = blocks;
+    return blocks;
+}
+
+static int64_t fill_ytable(const BatchState &b, const std::vector<int> &vols, const AxisKernels *k, int shape,
+                    MultiTable<YArgs> *t)
+{
+    t->nvol = (int)vols.size();
+    int64_t blocks = 0;
+    const int B = k->yzv[shape].B;
+    for (int i = 0; i < t->nvol; ++i) {
+        cubic_rl_plan_s *p = b.plans[vols[i]];
+        t->args[i] = y_args(p, p->ws, 0, 0, p->xh);
+        t->prefix[i] = blocks;
+        blocks += (p->xh + B - 1) / B * p->nz;
+    }
+    t->prefix[t->nvol] = blocks;
+    return blocks;
+}
+
+static int64_t fill_ztable(const BatchState &b, const std::vector<int> &vols, const AxisKernels *k, int shape,
+                    MultiTable<ZArgs> *t)
+{
+    t->nvol = (int)vols.size();
+    int64_t blocks = 0;
+    const int B = k->yzv[shape].B;
+    for (int i = 0; i < t->nvol; ++i) {
+        cubic_rl_plan_s *p = b.plans[vols[i]];
+        t->args[i] = z_args(p, p->ws, ZM_CONV, 1.f, 0, p->xh);
+        t->prefix[i] = blocks;
+        blocks += (p->xh + B - 1) / B * p->ny;
+    }
+    t->prefix[t->nvol] = blocks;
+    return blocks;
+}
+
+using LenGroups = std::map<int64_t, std::vector<int>>;
+
+// Times every candidate shape of every group whose length has no chosen shape yet, on
+// the batch's own buffers, and records the fastest: X by a ratio and an update launch, Y
+// by a forward and an inverse, Z by one product.  The buffers are left with arbitrary
+// finite contents; the batched run starts from its images anyway.
+static cubic_status_t batch_tune(BatchState &b, const LenGroups &byx, const LenGroups &byy, const LenGroups &byz,
+                          cudaStream_t st)
+{
+    auto known = [&](int64_t len, int pass) {
+        std::lock_guard<std::mutex> lk(g_bshape_mu);
+        return g_bshape.count({len, pass}) > 0;
+    };
+    bool any = false;
+    for (auto &kv : byx) any |= !known(kv.first, 0);
+    for (auto &kv : byy) any |= !known(kv.first, 1);
+    for (auto &kv : byz) any |= !known(kv.first, 2);
+    if (!any) return CUBIC_OK;
+    // finite data everywhere: each volume's start and the spectrum of it
+    for (size_t v = 0; v < b.plans.size(); ++v) {
+        cubic_rl_plan_s *p = b.plans[v];
+        cubic_status_t s = enqueue_init(p, b.images[v], b.eps, b.outs[v], st);
+        if (s != CUBIC_OK) return s;
+        if ((s = enqueue_forward3(p, b.outs[v], p->ws, 1.f / (float)p->V, st)) != CUBIC_OK) return s;
+    }
+    const size_t tsz = std::max({sizeof(MultiTable<XArgs>), sizeof(MultiTable<YArgs>), sizeof(MultiTable<ZArgs>)});
+    std::vector<unsigned char> host(tsz, 0);
+    void *dtab = nullptr;
+    CUBIC_CUDA(cudaMalloc(&dtab, tsz));
+    auto nothing = []() -> cubic_status_t { return CUBIC_OK; };
+    cubic_status_t s = CUBIC_OK;
+    auto upload = [&]() -> cubic_status_t {
+        CUBIC_CUDA(cudaMemcpyAsync(dtab, host.data(), tsz, cudaMemcpyHostToDevice, st));
+        return CUBIC_OK;
+    };
+    auto record = [&](int64_t len, int pass, int v) {
+        std::lock_guard<std::mutex> lk(g_bshape_mu);
+        g_bshape[{len, pass}] = v;
+    };
+    for (auto &kv : byx) {
+        if (s != CUBIC_OK || known(kv.first, 0)) continue;
+        const AxisKernels *k = find_axis(kv.first);
+        int best = default_xshape(k);
+        float best_ms = 1e30f;
+        for (int v = 0; v < k->nx && s == CUBIC_OK; ++v) {
+            auto *t = reinterpret_cast<MultiTable<XArgs> *>(host.data());
+            const int64_t blocks = fill_xtable(b, kv.second, k, v, t);
+            if ((s = upload()) != CUBIC_OK) break;
+            auto *tab = reinterpret_cast<const MultiTable<XArgs> *>(dtab);
+            float ms = 0.f;
+            s = time_best(st, nothing, [&]() -> cubic_status_t {
+                CUBIC_CUDA(k->xv[v].m[XM_RATIO](tab, blocks, st));
+                CUBIC_CUDA(k->xv[v].m[XM_UPDATE](tab, blocks, st));
+                return CUBIC_OK;
+            }, &ms);
+            if (ms < best_ms) { best_ms = ms; best = v; }
+        }
+        if (s == CUBIC_OK) record(kv.first, 0, best);
+    }
+    for (int pass = 1; pass <= 2 && s == CUBIC_OK; ++pass) {
+        for (auto &kv : (pass == 1 ? byy : byz)) {
+            if (s != CUBIC_OK || known(kv.first, pass)) continue;
+            const AxisKernels *k = find_axis(kv.first);
+            int best = default_yzshape(k);
+            float best_ms = 1e30f;
+            for (int v = 0; v < k->nyz && s == CUBIC_OK; ++v) {
+                if (!k->yzv[v].ym) continue;  // TMA variants have no multi-volume form
+                int64_t blocks;
+                if (pass == 1) blocks = fill_ytable(b, kv.second, k, v, reinterpret_cast<MultiTable<YArgs> *>(host.data()));
+                else blocks = fill_ztable(b, kv.second, k, v, reinterpret_cast<MultiTable<ZArgs> *>(host.data()));
+                if ((s = upload()) != CUBIC_OK) break;
+                float ms = 0.f;
+                s = time_best(st, nothing, [&]() -> cubic_status_t {
+                    if (pass == 1) {
+                        auto *tab = reinterpret_cast<const MultiTable<YArgs> *>(dtab);
+                        CUBIC_CUDA(k->yzv[v].ym(tab, blocks, 0, st));
+                        CUBIC_CUDA(k->yzv[v].ym(tab, blocks, 1, st));
+                    } else {
+                        auto *tab = reinterpret_cast<const MultiTable<ZArgs> *>(dtab);
+                        CUBIC_CUDA(k->yzv[v].zm(tab, blocks, ZM_CONV, st));
+                    }
+                    return CUBIC_OK;
+                }, &ms);
+                if (ms < best_ms) { best_ms = ms; best = v; }
+            }
+            if (s == CUBIC_OK) record(kv.first, pass, best);
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(dtab);
+    return s;
+}
+
+// Group volumes by axis length, tune the launch shapes of new lengths, and build the
+// device tables.
+static cubic_status_t build_batch(BatchState &b, cudaStream_t st)
 {
     const int n = (int)b.plans.size();
-    std::map<int64_t, std::vector<int>> byx, byy, byz;
+    LenGroups byx, byy, byz;
     for (int v = 0; v < n; ++v) {
         byx[b.plans[v]->nx].push_back(v);
         byy[b.plans[v]->ny].push_back(v);
         byz[b.plans[v]->nz].push_back(v);
     }
+    cubic_status_t s = batch_tune(b, byx, byy, byz, st);
+    if (s != CUBIC_OK) return s;
     const size_t ntab = byx.size() + byy.size() + byz.size();
     const size_t tsz = std::max({sizeof(MultiTable<XArgs>), sizeof(MultiTable<YArgs>), sizeof(MultiTable<ZArgs>)});
     const size_t stride = (tsz + 255) / 256 * 256;
@@ -2430,56 +2620,27 @@ static cubic_status_t build_batch(BatchState &b)
     unsigned char *dbase = (unsigned char *)b.dmem;
     size_t slot = 0;
     for (auto &kv : byx) {
-        auto *t = reinterpret_cast<MultiTable<XArgs> *>(host.data() + slot * stride);
         const AxisKernels *k = find_axis(kv.first);
-        t->nvol = (int)kv.second.size();
-        int64_t blocks = 0;
-        for (int i = 0; i < t->nvol; ++i) {
-            cubic_rl_plan_s *p = b.plans[kv.second[i]];
-            XArgs a = x_args(p);
-            a.spec_in = p->ws;
-            a.spec_out = p->ws;
-            a.src = b.outs[kv.second[i]];
-            a.u = b.outs[kv.second[i]];
-            a.dst = b.outs[kv.second[i]];
-            a.d = b.images[kv.second[i]];
-            a.eps = b.eps;
-            t->args[i] = a;
-            t->prefix[i] = blocks;
-            blocks += ((p->rows + 1) / 2 + k->xm_lines - 1) / k->xm_lines;
-        }
-        t->prefix[t->nvol] = blocks;
-        b.gx.push_back({k, reinterpret_cast<MultiTable<XArgs> *>(dbase + slot * stride), blocks});
+        const int shape = chosen_shape(kv.first, 0, default_xshape(k));
+        const int64_t blocks =
+            fill_xtable(b, kv.second, k, shape, reinterpret_cast<MultiTable<XArgs> *>(host.data() + slot * stride));
+        b.gx.push_back({k, reinterpret_cast<MultiTable<XArgs> *>(dbase + slot * stride), blocks, shape});
         ++slot;
     }
     for (auto &kv : byy) {
-        auto *t = reinterpret_cast<MultiTable<YArgs> *>(host.data() + slot * stride);
         const AxisKernels *k = find_axis(kv.first);
-        t->nvol = (int)kv.second.size();
-        int64_t blocks = 0;
-        for (int i = 0; i < t->nvol; ++i) {
-            cubic_rl_plan_s *p = b.plans[kv.second[i]];
-            t->args[i] = y_args(p, p->ws, 0, 0, p->xh);
-            t->prefix[i] = blocks;
-            blocks += (p->xh + k->m_cols - 1) / k->m_cols * p->nz;
-        }
-        t->prefix[t->nvol] = blocks;
-        b.gy.push_back({k, reinterpret_cast<MultiTable<YArgs> *>(dbase + slot * stride), blocks});
+        const int shape = chosen_shape(kv.first, 1, default_yzshape(k));
+        const int64_t blocks =
+            fill_ytable(b, kv.second, k, shape, reinterpret_cast<MultiTable<YArgs> *>(host.data() + slot * stride));
+        b.gy.push_back({k, reinterpret_cast<MultiTable<YArgs> *>(dbase + slot * stride), blocks, shape});
         ++slot;
     }
     for (auto &kv : byz) {
-        auto *t = reinterpret_cast<MultiTable<ZArgs> *>(host.data() + slot * stride);
         const AxisKernels *k = find_axis(kv.first);
-        t->nvol = (int)kv.second.size();
-        int64_t blocks = 0;
-        for (int i = 0; i < t->nvol; ++i) {
-            cubic_rl_plan_s *p = b.plans[kv.second[i]];
-            t->args[i] = z_args(p, p->ws, ZM_CONV, 1.f, 0, p->xh);
-            t->prefix[i] = blocks;
-            blocks += (p->xh + k->m_cols - 1) / k->m_cols * p->ny;
-        }
-        t->prefix[t->nvol] = blocks;
-        b.gz.push_back({k, reinterpret_cast<MultiTable<ZArgs> *>(dbase + slot * stride), blocks});
+        const int shape = chosen_shape(kv.first, 2, default_yzshape(k));
+        const int64_t blocks =
+            fill_ztable(b, kv.second, k, shape, reinterpret_cast<MultiTable<ZArgs> *>(host.data() + slot * stride));
+        b.gz.push_back({k, reinterpret_cast<MultiTable<ZArgs> *>(dbase + slot * stride), blocks, shape});
         ++slot;
     }
     CUBIC_CUDA(cudaMemcpy(b.dmem, host.data(), host.size(), cudaMemcpyHostToDevice));
@@ -2528,7 +2689,7 @@ extern "C" cubic_status_t cubic_rl_deconvolve_batched(const cubic_rl_plan_t *pla
         b->outs.assign(outs, outs + n);
         b->n_iter = n_iter;
         b->eps = eps;
-        cubic_status_t s = build_batch(*b);
+        cubic_status_t s = build_batch(*b, st);
         // capture the sequence on a private stream, then keep the instantiated graph
         cudaStream_t cap = nullptr;
         if (s == CUBIC_OK && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)

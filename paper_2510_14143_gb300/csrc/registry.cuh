@@ -31,6 +31,7 @@ constexpr int kMaxVariants = 8;
 struct XVariant {
     int P = 0, L = 0;
     XLaunch fn[XM_COUNT] = {};
+    XMultiLaunch m[XM_COUNT] = {};  // the same kernels over a table of volumes
 };
 
 struct YZVariant {
@@ -38,6 +39,10 @@ struct YZVariant {
     bool tma = false;  // persistent TMA-pipelined kernel
     YLaunch y = nullptr;
     ZLaunch z = nullptr;
+    // plain variants: the same kernels over a table of volumes (null for TMA variants,
+    // whose tensor maps are per volume)
+    YMultiLaunch ym = nullptr;
+    ZMultiLaunch zm = nullptr;
 };
 
 struct AxisKernels {
@@ -362,6 +367,11 @@ XVariant make_xvariant()
     v.fn[XM_RATIO] = launch_x<N, P, L, XM_RATIO>;
     v.fn[XM_UPDATE] = launch_x<N, P, L, XM_UPDATE>;
     v.fn[XM_FINAL] = launch_x<N, P, L, XM_FINAL>;
+    v.m[XM_FWD] = launch_x_multi<N, P, L, XM_FWD>;
+    v.m[XM_INV] = launch_x_multi<N, P, L, XM_INV>;
+    v.m[XM_RATIO] = launch_x_multi<N, P, L, XM_RATIO>;
+    v.m[XM_UPDATE] = launch_x_multi<N, P, L, XM_UPDATE>;
+    v.m[XM_FINAL] = launch_x_multi<N, P, L, XM_FINAL>;
     return v;
 }
 
@@ -373,6 +383,8 @@ YZVariant make_yzvariant()
     v.B = B;
     v.y = launch_y<N, P, B>;
     v.z = launch_z<N, P, B>;
+    v.ym = launch_y_multi<N, P, B>;
+    v.zm = launch_z_multi<N, P, B>;
     return v;
 }
 
