@@ -167,8 +167,12 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+_truth = {}
+
+
 def make_inputs(w: synth.Workload):
-    d, _ = synth.workload_volume(w)
+    d, x_true = synth.workload_volume(w)
+    _truth[w.name] = x_true      # the ground-truth object, for the metric legs
     return d
 
 
@@ -276,6 +280,8 @@ def run_ours(args, w: synth.Workload):
     }
     if not args.no_accel:
         result["accel"] = run_accel(cr, args, plan, d, n_iter, eps, ms / args.steps / n_iter)
+    if not args.no_metrics:
+        result["metrics"] = run_metrics(cr, args, plan, d, w, ms / args.steps / n_iter)
     if not args.no_paper_shape:
         result["paper_shape"] = run_paper_shape(cr, args)
     if not args.no_batched:
@@ -398,6 +404,47 @@ def run_accel(cr, args, plan, d, n_iter: int, eps: float, plain_ms_per_iter: flo
         res["time_to_same_nll_speedup"] = [round(lower * plain_ms_per_iter / ms, 3),
                                            round(match * plain_ms_per_iter / ms, 3)]
     return res
+
+
+def run_metrics(cr, args, plan, d, w: synth.Workload, plain_ms_per_iter: float):
+    """The metric rows on the timed volume, against its ground-truth object: RL with
+    metric-guided stopping on the scale-invariant PSNR (tol 0: stop once the PSNR falls),
+    its cost per iteration next to plain RL's, and the FSC of the result and the truth."""
+    import torch
+    truth = torch.from_numpy(_truth[w.name]).cuda()
+    out = torch.empty_like(d)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cr.cubic_rl_deconvolve_monitor(plan, d, 3, 1e-6, cr.METRIC_PSNR, -1.0, 1, out, truth)   # warm-up
+    torch.cuda.synchronize()
+    e0.record(stream)
+    n, hist = cr.cubic_rl_deconvolve_monitor(plan, d, 200, 1e-6, cr.METRIC_PSNR, 0.0, 1, out, truth)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    psnr = [h[2] for h in hist]
+    best = int(np.argmax(psnr))
+    n_shells = 64
+    fsc = torch.empty(n_shells, dtype=torch.float32, device="cuda")
+    cr.cubic_fsc(plan, out, truth, n_shells, fsc)
+    torch.cuda.synchronize()
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        cr.cubic_fsc(plan, out, truth, n_shells, fsc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fsc = e0.elapsed_time(e1) / reps
+    f = fsc.cpu().numpy()
+    below = np.nonzero(f < 1.0 / 7.0)[0]
+    V = int(d.numel())
+    return {"workload": f"the timed volume against its ground-truth object ({w.name})",
+            "psnr_stop": {"iterations": n, "ms": round(ms, 3), "ms_per_iter": round(ms / max(n, 1), 4),
+                          "plain_ms_per_iter": round(plain_ms_per_iter, 4), "best_psnr_db": round(psnr[best], 3),
+                          "best_iteration": best + 1, "psnr_db_first": round(psnr[0], 3),
+                          "rule": "stop at the first iteration whose scale-invariant PSNR falls"},
+            "fsc": {"n_shells": n_shells, "ms": round(ms_fsc, 3), "Gvoxel_per_s": round(V / (ms_fsc * 1e-3) / 1e9, 3),
+                    "first_shell_below_1_7": int(below[0]) if below.size else None}}
 
 
 def run_paper_shape(cr, args):
@@ -684,6 +731,7 @@ def main():
     ap.add_argument("--no-grad", action="store_true", help="skip the forward+backward leg")
     ap.add_argument("--no-accel", action="store_true", help="skip the accelerated-RL leg")
     ap.add_argument("--no-paper-shape", action="store_true", help="skip the 2560x2160x30 leg")
+    ap.add_argument("--no-metrics", action="store_true", help="skip the stopping-metric and FSC leg")
     ap.add_argument("--ncu-target", metavar="VX,VY,VZ",
                     help="profiling target only: plan + --ncu-iters RL iterations with these launch shapes")
     ap.add_argument("--ncu-iters", type=int, default=1)
