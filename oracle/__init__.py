@@ -70,6 +70,7 @@ def _load():
                 "orc_rl": ([P, P, i64, i64, i64, ci, cd, P], ci),
                 "orc_rl_grad": ([P, P, i64, i64, i64, ci, cd, P, P, P], ci),
                 "orc_fsc": ([P, P, i64, i64, i64, ci, P, P, P, P], ci),
+                "orc_fsc_split": ([P, i64, i64, i64, ci, P], ci),
                 "orc_rl_auto": ([P, P, i64, i64, i64, ci, cd, cd, ci, P, ctypes.POINTER(ci), P], ci),
                 "orc_rl_accel": ([P, P, i64, i64, i64, ci, cd, P, P], ci),
                 "orc_poisson_nll": ([P, P, i64, cd], cd),
@@ -284,6 +285,14 @@ def fsc(a, b, n_shells: int):
     outs = [np.zeros(int(n_shells), np.float64) for _ in range(4)]
     _check(_load().orc_fsc(_p(aa), _p(bb), *aa.shape, int(n_shells), *[_p(o) for o in outs]), "fsc")
     return tuple(outs)
+
+
+def fsc_split(d, n_shells: int) -> np.ndarray:
+    """Single-image FSC: mean FSC of the four opposite-parity pairs of sub-volumes."""
+    dd = _f64(d)
+    out = np.zeros(int(n_shells), np.float64)
+    _check(_load().orc_fsc_split(_p(dd), *dd.shape, int(n_shells), _p(out)), "fsc_split")
+    return out
 
 
 def rl_grad(d, psf, n_iter: int, eps: float, g_out):

@@ -845,6 +845,39 @@ int orc_fsc(const double *a, const double *b, int64_t nz, int64_t ny, int64_t nx
     return rc;
 }
 
+/* Single-image FSC (the paper's resolution metric computed from one image, Section 4,
+ * "Evaluation metrics", citing Koho et al. 2019): the volume (even dims) splits into its
+ * eight parity sub-volumes s_abc(z, y, x) = d(2z + a, 2y + b, 2x + c); the FSC of each of
+ * the four pairs of opposite parity (abc with (1-a)(1-b)(1-c)) is taken on the half grid
+ * and the four curves are averaged shell by shell.  Readings: plain mean of the four
+ * pairs; no correction for the half-voxel diagonal shift between a pair; shells are
+ * those of the half grid (its Nyquist is half the full grid's).  out: n_shells values. */
+int orc_fsc_split(const double *d, int64_t nz, int64_t ny, int64_t nx, int n_shells, double *out)
+{
+    if (!d || !out || nz < 2 || ny < 2 || nx < 2 || nz % 2 || ny % 2 || nx % 2 || n_shells < 1) return -1;
+    const int64_t hz = nz / 2, hy = ny / 2, hx = nx / 2, H = hz * hy * hx;
+    double *a = malloc(sizeof(double) * (size_t)H), *b = malloc(sizeof(double) * (size_t)H);
+    double *f = malloc(sizeof(double) * (size_t)n_shells);
+    int rc = (a && b && f) ? 0 : -2;
+    for (int s = 0; s < n_shells; ++s) out[s] = 0.0;
+    for (int pair = 0; pair < 4 && !rc; ++pair) {
+        /* one half has z-parity 0 and (y, x) parities from the pair index; the other the
+         * complementary parities */
+        const int p0[3] = {0, (pair >> 1) & 1, pair & 1};
+        for (int64_t z = 0; z < hz; ++z)
+            for (int64_t y = 0; y < hy; ++y)
+                for (int64_t x = 0; x < hx; ++x) {
+                    const int64_t i = (z * hy + y) * hx + x;
+                    a[i] = d[((2 * z + p0[0]) * ny + 2 * y + p0[1]) * nx + 2 * x + p0[2]];
+                    b[i] = d[((2 * z + 1 - p0[0]) * ny + 2 * y + 1 - p0[1]) * nx + 2 * x + 1 - p0[2]];
+                }
+        rc = orc_fsc(a, b, hz, hy, hx, n_shells, f, NULL, NULL, NULL);
+        for (int s = 0; s < n_shells && !rc; ++s) out[s] += 0.25 * f[s];
+    }
+    free(a); free(b); free(f);
+    return rc;
+}
+
 /* Reverse mode through n_iter RL iterations.
  * g_out = dL/du_K.  Writes grad_d = dL/dd (through the ratio at every
  * iteration and through u0 = max(mean(d), eps)) and grad_psf = dL/dp for the

@@ -772,3 +772,30 @@ def test_rl_accel_same_composition():
     x, a = oracle.rl_accel_same(d, psf, 10, 1e-6)
     assert abs(x.sum() - d.sum()) <= 1e-11 * d.sum() and x.min() >= 0
     assert np.all((a >= 0) & (a <= 1)) and a[2:].max() > 0.3
+
+
+# ------------------------------------------------------------ single-image FSC
+
+def test_fsc_split_block_constant_and_checkerboard():
+    r = np.random.default_rng(97)
+    # every 2x2x2 block constant: the eight parity sub-volumes are identical
+    base = r.uniform(1, 5, (4, 5, 6))
+    d = np.repeat(np.repeat(np.repeat(base, 2, 0), 2, 1), 2, 2)
+    f = oracle.fsc_split(d, 6)
+    _, num, _, _ = oracle.fsc(base, base, 6)
+    assert np.allclose(f[num != 0], 1.0, atol=1e-12) and np.all(f[num == 0] == 0.0)
+    # c + A (-1)^(z+y+x): each sub-volume is a constant, opposite ones c + A and c - A, so
+    # the DC shell holds sign(c^2 - A^2) (the other shells carry only rounding noise)
+    z, y, x = np.meshgrid(np.arange(8), np.arange(10), np.arange(12), indexing="ij")
+    for c, A, sign in ((3.0, 1.0, 1.0), (1.0, 3.0, -1.0)):
+        f = oracle.fsc_split(c + A * (-1.0) ** (z + y + x), 4)
+        assert np.isclose(f[0], sign, atol=1e-12) and np.all(np.abs(f) <= 1.0 + 1e-12)
+
+
+def test_fsc_split_matches_sliced_pairs():
+    d = np.random.default_rng(98).uniform(0, 1, (8, 12, 10))
+    ref = np.zeros(5)
+    for b in (0, 1):
+        for c in (0, 1):
+            ref += 0.25 * oracle.fsc(d[0::2, b::2, c::2], d[1::2, 1 - b::2, 1 - c::2], 5)[0]
+    assert np.allclose(oracle.fsc_split(d, 5), ref, atol=1e-13)
