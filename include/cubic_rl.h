@@ -270,6 +270,17 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve_auto(cubic_rl_plan_t plan, const fl
 CUBIC_API cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const float *b, int n_shells,
                                    float *fsc, void *stream);
 
+/* Single-image FSC (the resolution measure of the paper's Section 4 "Evaluation metrics",
+ * computed from one image after Koho et al. 2019).  image: device float32 of dims 2h =
+ * {2 hz, 2 hy, 2 hx}; half_plan: a plan (circular) of dims h, whose PSF is not used.  The
+ * image splits into its eight parity sub-volumes d(2z + a, 2y + b, 2x + c); the FSC of each
+ * of the four pairs of opposite parity is taken on the half grid (shells of the half grid)
+ * and fsc (device float[n_shells]) receives their mean.  No correction is made for the
+ * half-voxel diagonal shift within a pair.  Uses a small stream-ordered scratch allocation.
+ * Errors: INVALID_ARG, ALIGNMENT, OUT_OF_MEMORY, CUDA. */
+CUBIC_API cubic_status_t cubic_fsc_split(cubic_rl_plan_t half_plan, const float *image, int n_shells, float *fsc,
+                                         void *stream);
+
 /* ---- differentiation (reverse mode through the iterations) ---- */
 
 /* cubic_rl_deconvolve that also stores the estimate u_k at every k = 0, ckpt_every,

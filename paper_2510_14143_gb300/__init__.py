@@ -66,6 +66,7 @@ _SIGS = {
                                      _vp], _ci),
     "cubic_rl_batched_graph_nodes": ([], _i64),
     "cubic_fsc": ([_vp, _vp, _vp, _ci, _vp, _vp], _ci),
+    "cubic_fsc_split": ([_vp, _vp, _ci, _vp, _vp], _ci),
     "cubic_rl_deconvolve_auto": ([_vp, _vp, _ci, _cf, _cf, _ci, _vp, ctypes.POINTER(_ci),
                                   ctypes.POINTER(ctypes.c_double), _vp], _ci),
     "cubic_rl_deconvolve_accel": ([_vp, _vp, _ci, _cf, _vp, _vp, _vp], _ci),
@@ -369,6 +370,17 @@ def cubic_fsc(plan: Plan, a, b, n_shells: int, fsc=None, stream=None):
     _check(lib().cubic_fsc(plan.handle, _ptr(a, torch.float32, plan.voxels, "a"),
                            _ptr(b, torch.float32, plan.voxels, "b"), int(n_shells),
                            _ptr(fsc, torch.float32, int(n_shells), "fsc"), _stream(stream)), "cubic_fsc")
+    return fsc
+
+
+def cubic_fsc_split(half_plan: Plan, image, n_shells: int, fsc=None, stream=None):
+    """Single-image FSC of a volume of twice the plan's dims; returns the float32 CUDA tensor."""
+    import torch
+    if fsc is None:
+        fsc = torch.empty(int(n_shells), dtype=torch.float32, device="cuda")
+    _check(lib().cubic_fsc_split(half_plan.handle, _ptr(image, torch.float32, 8 * half_plan.voxels, "image"),
+                                 int(n_shells), _ptr(fsc, torch.float32, int(n_shells), "fsc"), _stream(stream)),
+           "cubic_fsc_split")
     return fsc
 
 

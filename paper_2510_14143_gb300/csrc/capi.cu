@@ -2294,15 +2294,9 @@ __global__ void k_fsc_final(const float *__restrict__ sums, int S, float *__rest
     }
 }
 
-extern "C" cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const float *b, int n_shells, float *fsc,
-                                    void *stream)
+// The FSC's scratch: a second spectrum and the shell sums
+static cubic_status_t ensure_fsc(cubic_rl_plan_s *p)
 {
-    if (!plan || !a || !b || !fsc) return fail(CUBIC_ERR_INVALID_ARG, "plan, a, b and fsc must be non-null");
-    if (cubic_status_t g = no_linear(plan, "FSC")) return g;
-    if (n_shells < 1 || n_shells > kFscMaxShells)
-        return fail(CUBIC_ERR_INVALID_ARG, "n_shells must be in [1, %d]", kFscMaxShells);
-    if (!aligned16(a) || !aligned16(b)) return fail(CUBIC_ERR_ALIGNMENT, "a and b must be 16-byte aligned");
-    cubic_rl_plan_s *p = plan;
     cubic_status_t s = ensure_workspace(p);
     if (s != CUBIC_OK) return s;
     if (!p->ws2) {
@@ -2310,7 +2304,7 @@ extern "C" cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const 
         CUBIC_CUDA(cudaMalloc(&m, spec_elems(p) * sizeof(float2)));
         p->ws2 = (float2 *)m;
     }
-    if (p->fsc_cap < n_shells) {
+    if (p->fsc_cap < kFscMaxShells) {
         cudaDeviceSynchronize();
         cudaFree(p->fsc_sums);
         p->fsc_sums = nullptr;
@@ -2320,7 +2314,13 @@ extern "C" cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const 
         p->fsc_sums = (float *)m;
         p->fsc_cap = kFscMaxShells;
     }
-    cudaStream_t st = (cudaStream_t)stream;
+    return CUBIC_OK;
+}
+
+static cubic_status_t enqueue_fsc(cubic_rl_plan_s *p, const float *a, const float *b, int n_shells, float *fsc,
+                                  cudaStream_t st)
+{
+    cubic_status_t s;
     if ((s = enqueue_forward3(p, a, p->ws, 1.f, st)) != CUBIC_OK) return s;
     if ((s = enqueue_forward3(p, b, p->ws2, 1.f, st)) != CUBIC_OK) return s;
     CUBIC_CUDA(cudaMemsetAsync(p->fsc_sums, 0, 6 * (size_t)n_shells * sizeof(float), st));
@@ -2329,6 +2329,68 @@ extern "C" cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const 
     k_fsc_final<<<(n_shells + 255) / 256, 256, 0, st>>>(p->fsc_sums, n_shells, fsc);
     CUBIC_CUDA(cudaGetLastError());
     return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_fsc(cubic_rl_plan_t plan, const float *a, const float *b, int n_shells, float *fsc,
+                                    void *stream)
+{
+    if (!plan || !a || !b || !fsc) return fail(CUBIC_ERR_INVALID_ARG, "plan, a, b and fsc must be non-null");
+    if (cubic_status_t g = no_linear(plan, "FSC")) return g;
+    if (n_shells < 1 || n_shells > kFscMaxShells)
+        return fail(CUBIC_ERR_INVALID_ARG, "n_shells must be in [1, %d]", kFscMaxShells);
+    if (!aligned16(a) || !aligned16(b)) return fail(CUBIC_ERR_ALIGNMENT, "a and b must be 16-byte aligned");
+    cubic_status_t s = ensure_fsc(plan);
+    if (s != CUBIC_OK) return s;
+    return enqueue_fsc(plan, a, b, n_shells, fsc, (cudaStream_t)stream);
+}
+
+// Single-image FSC: the sub-volumes of opposite parity, pair `pair` (z-parity 0 and
+// (y, x) parities from its bits against the complementary parities), of a volume of
+// dims 2h into a and b of dims h
+__global__ void k_split_pair(const float *__restrict__ d, float *__restrict__ a, float *__restrict__ b, int64_t hz,
+                             int64_t hy, int64_t hx, int pair)
+{
+    const int py = (pair >> 1) & 1, px = pair & 1;
+    const int64_t ny = 2 * hy, nx = 2 * hx, H = hz * hy * hx;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < H; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i % hx, y = (i / hx) % hy, z = i / (hx * hy);
+        a[i] = d[((2 * z) * ny + 2 * y + py) * nx + 2 * x + px];
+        b[i] = d[((2 * z + 1) * ny + 2 * y + 1 - py) * nx + 2 * x + 1 - px];
+    }
+}
+
+// fsc[s] = the mean of the four curves in curves[4][S]
+__global__ void k_mean4(const float *__restrict__ curves, int S, float *__restrict__ fsc)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x)
+        fsc[s] = 0.25f * (curves[s] + curves[S + s] + curves[2 * S + s] + curves[3 * S + s]);
+}
+
+extern "C" cubic_status_t cubic_fsc_split(cubic_rl_plan_t half_plan, const float *image, int n_shells, float *fsc,
+                                          void *stream)
+{
+    if (!half_plan || !image || !fsc) return fail(CUBIC_ERR_INVALID_ARG, "plan, image and fsc must be non-null");
+    if (cubic_status_t g = no_linear(half_plan, "FSC")) return g;
+    if (n_shells < 1 || n_shells > kFscMaxShells)
+        return fail(CUBIC_ERR_INVALID_ARG, "n_shells must be in [1, %d]", kFscMaxShells);
+    if (!aligned16(image)) return fail(CUBIC_ERR_ALIGNMENT, "image must be 16-byte aligned");
+    cubic_rl_plan_s *p = half_plan;
+    cubic_status_t s = ensure_fsc(p);
+    if (s != CUBIC_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t hb = ((size_t)p->V * sizeof(float) + 255) / 256 * 256;
+    const size_t cb = (4 * (size_t)n_shells * sizeof(float) + 255) / 256 * 256;
+    void *m = nullptr;
+    CUBIC_CUDA(cudaMallocAsync(&m, 2 * hb + cb, st));
+    float *a = (float *)m, *b = (float *)((unsigned char *)m + hb), *curves = (float *)((unsigned char *)m + 2 * hb);
+    for (int pair = 0; pair < 4 && s == CUBIC_OK; ++pair) {
+        k_split_pair<<<grid_for(p->V, 256), 256, 0, st>>>(image, a, b, p->nz, p->ny, p->nx, pair);
+        s = enqueue_fsc(p, a, b, n_shells, curves + (size_t)pair * n_shells, st);
+    }
+    if (s == CUBIC_OK) k_mean4<<<(n_shells + 255) / 256, 256, 0, st>>>(curves, n_shells, fsc);
+    cudaFreeAsync(m, st);
+    if (s == CUBIC_OK) CUBIC_CUDA(cudaGetLastError());
+    return s;
 }
 
 // ------------------------------------------------------------------ batched deconvolution
