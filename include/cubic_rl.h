@@ -7,7 +7,8 @@
  * the PSF (convolution with the flipped PSF) and multiplies the estimate by the result.
  * The same section fixes the PSF to the image's ZYX size and does the convolutions with
  * FFTs.  Readings taken where the paper is silent:
- *   - boundaries are circular (same-size FFT convolution, no padding);
+ *   - boundaries are circular (same-size FFT convolution, no padding), except for plans
+ *     made by cubic_rl_plan_linear (zero-padded "same"-mode convolution);
  *   - the PSF peak sits at index floor(n/2) on every axis;
  *   - the initial estimate is the constant max(mean(image), eps);
  *   - the ratio's denominator is clamped: image / max(blurred, eps).
@@ -104,10 +105,13 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve(cubic_rl_plan_t plan, const float *
  * possibly different sizes, each with its own plan (plans must be distinct: a plan's scratch
  * serves one volume).  images[v], outs[v]: device float32 volumes of plans[v]'s dims.  For
  * each pass, all volumes with the same length along that pass share one kernel launch whose
- * blocks span every member volume; the whole n_iter sequence is captured once into a CUDA
- * graph (first call with a given argument set: capture + instantiation, synchronous) and
- * replayed on `stream` by later calls with identical arguments (a few argument sets are
- * cached).  1 <= n <= 256.  Errors: INVALID_ARG, ALIGNMENT, OUT_OF_MEMORY, CUDA. */
+ * blocks span every member volume.  The launch shape of each such launch (threads per line,
+ * lines or columns per CTA) is tuned the first time a length appears: every candidate is
+ * timed on the call's own buffers and the fastest is kept for the process.  The whole
+ * n_iter sequence is captured once into a CUDA graph (first call with a given argument
+ * set: tuning of new lengths, capture and instantiation, synchronous) and replayed on
+ * `stream` by later calls with identical arguments (a few argument sets are cached).
+ * 1 <= n <= 256.  Errors: INVALID_ARG, ALIGNMENT, OUT_OF_MEMORY, CUDA. */
 CUBIC_API cubic_status_t cubic_rl_deconvolve_batched(const cubic_rl_plan_t *plans, int n,
                                                      const float *const *images, int n_iter, float eps,
                                                      float *const *outs, void *stream);
@@ -134,9 +138,8 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve_host(cubic_rl_plan_t plan, const fl
  * cubic_rl_deconvolve, cubic_rl_deconvolve_host, cubic_rl_deconvolve_accel,
  * cubic_rl_deconvolve_auto, cubic_rl_convolve, cubic_rl_plan_update_psf (psf of psf_dims),
  * cubic_rl_autotune and the plan queries.  Every other entry point returns INVALID_ARG
- * for it.  Errors: INVALID_ARG,
- * UNSUPPORTED_SIZE (no supported length, or padded nz or ny above 65535), ALIGNMENT,
- * OUT_OF_MEMORY, CUDA. */
+ * for it.  Errors: INVALID_ARG, UNSUPPORTED_SIZE (no supported length, or padded nz or
+ * ny above 65535), ALIGNMENT, OUT_OF_MEMORY, CUDA. */
 CUBIC_API cubic_status_t cubic_rl_plan_linear(cubic_rl_plan_t *plan, const int64_t dims[3],
                                               const int64_t psf_dims[3], const float *psf, unsigned flags,
                                               void *stream);
@@ -338,10 +341,11 @@ CUBIC_API cubic_status_t cubic_rl_profile_read(cubic_rl_plan_t plan, int n_kinds
 
 /* ---- building blocks (the same kernels, exposed for the forward model and for tests) ---- */
 
-/* Circular convolution with the plan's PSF (the blur step of Section 4 of the paper):
- * out = psf (*) in.  flipped != 0 gives the correlation with the PSF (a convolution with
- * the mirrored PSF, the step that carries the ratio back), the adjoint of the former.
- * in, out: device float32 [nz][ny][nx]; they may alias.  Uses the plan workspace. */
+/* Convolution with the plan's PSF (the blur step of Section 4 of the paper):
+ * out = psf (*) in, circular, or zero-padded "same"-mode for a cubic_rl_plan_linear plan.
+ * flipped != 0 gives the correlation with the PSF (a convolution with the mirrored PSF,
+ * the step that carries the ratio back), the adjoint of the former.  in, out: device
+ * float32 [nz][ny][nx] of the image dims; they may alias.  Uses the plan workspace. */
 CUBIC_API cubic_status_t cubic_rl_convolve(cubic_rl_plan_t plan, const float *in, int flipped, float *out,
                                  void *stream);
 
