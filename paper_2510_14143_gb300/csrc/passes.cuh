@@ -161,17 +161,27 @@ constexpr int x_smem_line()
 // The pointwise operand rows (d for the ratio, u for the update) are staged
 // into shared memory by one bulk TMA copy per CTA issued at kernel start, so
 // their HBM latency hides behind the inverse transform.  Needs 16-byte rows.
-template <int N, int MODE>
+// With PF (ratio and update only) they are instead prefetched into L2 at kernel
+// start and read from global memory: 2 N floats less shared memory per line pair,
+// so more CTAs fit on an SM.
+template <int N, int MODE, bool PF = false>
+constexpr bool x_prefetches()
+{
+    return PF && (MODE == XM_RATIO || MODE == XM_UPDATE) && (N % 4 == 0);
+}
+
+template <int N, int MODE, bool PF = false>
 constexpr bool x_uses_tma()
 {
-    return (MODE == XM_RATIO || MODE == XM_UPDATE || MODE == XM_FINAL) && (N % 4 == 0);
+    return (MODE == XM_RATIO || MODE == XM_UPDATE || MODE == XM_FINAL) && (N % 4 == 0) &&
+           !x_prefetches<N, MODE, PF>();
 }
 
 // shared memory: [2 mbarriers | operand rows (TMA modes) | stage twiddles | line-pair regions]
-template <int N, int P, int L, int MODE>
+template <int N, int P, int L, int MODE, bool PF = false>
 constexpr size_t x_smem_bytes()
 {
-    return 16 + (x_uses_tma<N, MODE>() ? (size_t)L * 2 * N * sizeof(float) : 0) +
+    return 16 + (x_uses_tma<N, MODE, PF>() ? (size_t)L * 2 * N * sizeof(float) : 0) +
            (size_t)((tw_table_size(N, N / P) + 1) / 2 * 2) * sizeof(float2) +
            (size_t)L * x_smem_line<N, P>() * sizeof(float2);
 }
@@ -233,11 +243,12 @@ __device__ __forceinline__ void slot_add(float *pair, CFloat v)
     catomic_add(pair, pair + 1, -v.c);
 }
 
-template <int N, int P, int L, int MODE>
+template <int N, int P, int L, int MODE, bool PF>
 __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
 {
     constexpr int E = N / P;
-    constexpr bool kTma = x_uses_tma<N, MODE>();
+    constexpr bool kTma = x_uses_tma<N, MODE, PF>();
+    constexpr bool kPf = x_prefetches<N, MODE, PF>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using FFT = LineFFT<N, P, true>;
     constexpr int XB = x_row_xb<N>();
@@ -263,6 +274,15 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     auto sync = [] { __syncthreads(); };
 
     pdl_trigger();
+    if constexpr (kPf) {
+        if (threadIdx.x == 0) {
+            // a hint only, so it may run before the wait: the loads below come after it
+            const int64_t row0 = block * L * 2;
+            const int64_t left = a.rows - row0;
+            const int64_t nrows = left < 2 * L ? left : 2 * L;
+            bulk_prefetch_l2((MODE == XM_RATIO ? a.d : a.u) + row0 * N, (unsigned)(nrows * N * sizeof(float)));
+        }
+    }
     FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * L);  // plan constant: before the wait
     if constexpr (kTma || kSpecIn) {
         if (threadIdx.x == 0) {
@@ -392,7 +412,16 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
                 const int slot = (int)((block * ((P * L + 31) / 32) + (threadIdx.x >> 5)) & 63);
                 slot_add<P * L>(a.nll_stats + 2 * slot, c_nll);
             }
-            static_for<0, E>([&](auto i_) {
+            if (kPf && !keep) {
+                // d from global memory: no store in this loop, so its loads issue together
+                static_for<0, E>([&](auto i_) {
+                    constexpr int i = CUBIC_CI(i_);
+                    const int n = t + P * i;
+                    const float x0 = ok0 ? __fdividef(__ldg(p0 + n), fmaxf(v[i].x, eps)) : 0.f;
+                    const float x1 = ok1 ? __fdividef(__ldg(p1 + n), fmaxf(v[i].y, eps)) : 0.f;
+                    v[i] = make_float2(x0, x1);
+                });
+            } else static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
                 // fast division (max 2 ulp for denominators below 2^126; the
@@ -430,7 +459,36 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
                     });
                 }
             }
-            static_for<0, E>([&](auto i_) {
+            if constexpr (kPf) {
+                // u from global memory, usually updated in place: every load of the
+                // loop below comes before the first store to u, so none waits behind one
+                if (keep) {
+                    static_for<0, E>([&](auto i_) {
+                        constexpr int i = CUBIC_CI(i_);
+                        const int n = t + P * i;
+                        if (ok0) kq0[n] = v[i].x;
+                        if (ok1) kq1[n] = v[i].y;
+                    });
+                }
+                static_for<0, E>([&](auto i_) {
+                    constexpr int i = CUBIC_CI(i_);
+                    const int n = t + P * i;
+                    const float u0v = ok0 ? p0[n] : 0.f, u1v = ok1 ? p1[n] : 0.f;
+                    const float x0 = ok0 ? u0v * v[i].x : 0.f;
+                    const float x1 = ok1 ? u1v * v[i].y : 0.f;
+                    if (stats) {
+                        s_num = fmaf(x0 - u0v, x0 - u0v, fmaf(x1 - u1v, x1 - u1v, s_num));
+                        s_den = fmaf(u0v, u0v, fmaf(u1v, u1v, s_den));
+                    }
+                    v[i] = make_float2(x0, x1);
+                });
+                static_for<0, E>([&](auto i_) {
+                    constexpr int i = CUBIC_CI(i_);
+                    const int n = t + P * i;
+                    if (ok0) o0[n] = v[i].x;
+                    if (ok1) o1[n] = v[i].y;
+                });
+            } else static_for<0, E>([&](auto i_) {
                 constexpr int i = CUBIC_CI(i_);
                 const int n = t + P * i;
                 const float u0v = ok0 ? p0[n] : 0.f, u1v = ok1 ? p1[n] : 0.f;
@@ -536,8 +594,8 @@ __device__ __forceinline__ int find_volume(const int64_t *prefix, int nvol, int6
 }
 
 // tab == nullptr: one volume, arguments by value.  Otherwise the volumes of tab.
-template <int N, int P, int L, int MODE>
-__global__ void __launch_bounds__(P * L) k_xpass(XArgs a, const MultiTable<XArgs> *tab)
+template <int N, int P, int L, int MODE, bool PF>
+__device__ __forceinline__ void x_entry(XArgs a, const MultiTable<XArgs> *tab)
 {
     int64_t block = blockIdx.x;
     if (tab) {
@@ -545,7 +603,32 @@ __global__ void __launch_bounds__(P * L) k_xpass(XArgs a, const MultiTable<XArgs
         a = tab->args[v];
         block -= tab->prefix[v];
     }
-    x_body<N, P, L, MODE>(a, block);
+    x_body<N, P, L, MODE, PF>(a, block);
+}
+
+template <int N, int P, int L, int MODE>
+__global__ void __launch_bounds__(P * L) k_xpass(XArgs a, const MultiTable<XArgs> *tab)
+{
+    x_entry<N, P, L, MODE, false>(a, tab);
+}
+
+// The prefetching ratio and update kernels exist to fit more CTAs on an SM: they are
+// held to the register count of 28 resident warps.
+template <int N, int P, int L, int MODE>
+__global__ void __launch_bounds__(P * L, (P * L <= 448 ? 896 / (P * L) : 1))
+    k_xpass_pf(XArgs a, const MultiTable<XArgs> *tab)
+{
+    x_entry<N, P, L, MODE, true>(a, tab);
+}
+
+// the kernel of one X launch shape
+template <int N, int P, int L, int MODE, bool PF>
+constexpr auto x_kernel()
+{
+    if constexpr (x_prefetches<N, MODE, PF>())
+        return k_xpass_pf<N, P, L, MODE>;
+    else
+        return k_xpass<N, P, L, MODE>;
 }
 
 // ------------------------------------------------------------------ Y pass

@@ -89,13 +89,13 @@ inline cudaError_t set_smem(const void *fn, size_t bytes)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int N, int P, int L, int MODE>
+template <int N, int P, int L, int MODE, bool PF = false>
 cudaError_t launch_x(const XArgs &a, cudaStream_t st)
 {
     const int64_t pairs = (a.rows + 1) / 2;
     const int64_t grid = (pairs + L - 1) / L;
-    constexpr size_t smem = x_smem_bytes<N, P, L, MODE>();
-    auto fn = k_xpass<N, P, L, MODE>;
+    constexpr size_t smem = x_smem_bytes<N, P, L, MODE, PF>();
+    auto fn = x_kernel<N, P, L, MODE, PF>();
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (grid == 0) return cudaSuccess;
@@ -323,11 +323,11 @@ constexpr int tma_stages()
     }
 }
 
-template <int N, int P, int L, int MODE>
+template <int N, int P, int L, int MODE, bool PF = false>
 cudaError_t launch_x_multi(const MultiTable<XArgs> *tab, int64_t blocks, cudaStream_t st)
 {
-    constexpr size_t smem = x_smem_bytes<N, P, L, MODE>();
-    auto fn = k_xpass<N, P, L, MODE>;
+    constexpr size_t smem = x_smem_bytes<N, P, L, MODE, PF>();
+    auto fn = x_kernel<N, P, L, MODE, PF>();
     static cudaError_t attr = set_smem((const void *)fn, smem);
     if (attr != cudaSuccess) return attr;
     if (blocks == 0) return cudaSuccess;
@@ -356,7 +356,9 @@ cudaError_t launch_z_multi(const MultiTable<ZArgs> *tab, int64_t blocks, int mod
     return launch_pdl(fn, dim3((unsigned)blocks), dim3(P * B), smem, st, ZArgs{}, tab, mode);
 }
 
-template <int N, int P, int L>
+// PR / PU: the ratio / update pass reads its operand rows through an L2 prefetch
+// instead of staging them in shared memory
+template <int N, int P, int L, bool PR = false, bool PU = false>
 XVariant make_xvariant()
 {
     XVariant v;
@@ -364,13 +366,13 @@ XVariant make_xvariant()
     v.L = L;
     v.fn[XM_FWD] = launch_x<N, P, L, XM_FWD>;
     v.fn[XM_INV] = launch_x<N, P, L, XM_INV>;
-    v.fn[XM_RATIO] = launch_x<N, P, L, XM_RATIO>;
-    v.fn[XM_UPDATE] = launch_x<N, P, L, XM_UPDATE>;
+    v.fn[XM_RATIO] = launch_x<N, P, L, XM_RATIO, PR>;
+    v.fn[XM_UPDATE] = launch_x<N, P, L, XM_UPDATE, PU>;
     v.fn[XM_FINAL] = launch_x<N, P, L, XM_FINAL>;
     v.m[XM_FWD] = launch_x_multi<N, P, L, XM_FWD>;
     v.m[XM_INV] = launch_x_multi<N, P, L, XM_INV>;
-    v.m[XM_RATIO] = launch_x_multi<N, P, L, XM_RATIO>;
-    v.m[XM_UPDATE] = launch_x_multi<N, P, L, XM_UPDATE>;
+    v.m[XM_RATIO] = launch_x_multi<N, P, L, XM_RATIO, PR>;
+    v.m[XM_UPDATE] = launch_x_multi<N, P, L, XM_UPDATE, PU>;
     v.m[XM_FINAL] = launch_x_multi<N, P, L, XM_FINAL>;
     return v;
 }
@@ -421,6 +423,15 @@ AxisKernels make_axis()
     // stages (2560: 40 x 8 x 8 instead of 20 x 4 x 4 x 4 x 2)
     constexpr int PW = N > 1024 ? choose_threads(N, 40) : -1;
     if constexpr (PW > 0 && PW != P0 && PW != S::P1) push_x(k, make_xvariant<N, PW, S::lines(PW, 128)>());
+    // long lines: the default split with the ratio and/or the update reading their
+    // operand rows through L2 (less shared memory per CTA, more CTAs per SM)
+    if constexpr (N >= 256 && N % 4 == 0) {
+        constexpr int PX = S::kAlt ? S::P1 : P0;
+        constexpr int LX = S::lines(PX, 128);
+        push_x(k, make_xvariant<N, PX, LX, true, true>());
+        push_x(k, make_xvariant<N, PX, LX, true, false>());
+        push_x(k, make_xvariant<N, PX, LX, false, true>());
+    }
     constexpr int XL = S::lines(P0, 128);
     k.xm[XM_FWD] = launch_x_multi<N, P0, XL, XM_FWD>;
     k.xm[XM_INV] = launch_x_multi<N, P0, XL, XM_INV>;

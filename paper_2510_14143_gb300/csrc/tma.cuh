@@ -51,6 +51,13 @@ __device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gsrc, unsig
         : "memory");
 }
 
+// Hint: start bringing `bytes` (multiple of 16, 16-byte aligned address) of global memory
+// into L2.  Nothing waits for it and it changes no value a later load sees.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *gsrc, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gsrc), "r"(bytes) : "memory");
+}
+
 // Programmatic dependent launch.  pdl_trigger: this CTA lets the next kernel in the
 // stream start launching (it runs only its constant prologue before pdl_wait).
 // pdl_wait: block until every grid this one depends on has completed and its memory
