@@ -613,9 +613,17 @@ __global__ void __launch_bounds__(P * L) k_xpass(XArgs a, const MultiTable<XArgs
 }
 
 // The prefetching ratio and update kernels exist to fit more CTAs on an SM: they are
-// held to the register count of 28 resident warps.
+// held to the register count of 28 resident warps (72 registers) for up to 16 elements
+// per thread, else of 16 warps (128 registers).
+template <int N, int P, int L>
+constexpr int x_pf_min_blocks()
+{
+    constexpr int threads = N / P <= 16 ? 896 : 512;
+    return P * L <= threads / 2 ? threads / (P * L) : 1;
+}
+
 template <int N, int P, int L, int MODE>
-__global__ void __launch_bounds__(P * L, (P * L <= 448 ? 896 / (P * L) : 1))
+__global__ void __launch_bounds__(P * L, (x_pf_min_blocks<N, P, L>()))
     k_xpass_pf(XArgs a, const MultiTable<XArgs> *tab)
 {
     x_entry<N, P, L, MODE, true>(a, tab);
