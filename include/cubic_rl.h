@@ -136,7 +136,8 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve_host(cubic_rl_plan_t plan, const fl
  * m >= max(n + floor(k/2), k) per axis, which is exact for this output.  The plan owns two
  * zero-padded copies of the image box (image and estimate).  Supported on such a plan:
  * cubic_rl_deconvolve, cubic_rl_deconvolve_host, cubic_rl_deconvolve_accel,
- * cubic_rl_deconvolve_auto, cubic_rl_convolve, cubic_rl_plan_update_psf (psf of psf_dims),
+ * cubic_rl_deconvolve_auto, cubic_rl_deconvolve_monitor (the likelihood summed over the
+ * image's voxels), cubic_rl_convolve, cubic_rl_plan_update_psf (psf of psf_dims),
  * cubic_rl_autotune and the plan queries.  Every other entry point returns INVALID_ARG
  * for it.  Errors: INVALID_ARG, UNSUPPORTED_SIZE (no supported length, or padded nz or
  * ny above 65535), ALIGNMENT, OUT_OF_MEMORY, CUDA. */

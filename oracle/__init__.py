@@ -79,6 +79,8 @@ def _load():
                 "orc_rl_accel_same": ([P, P, i64, i64, i64, i64, i64, i64, ci, cd, P, P], ci),
                 "orc_psnr_si": ([P, P, i64], cd),
                 "orc_rl_monitor": ([P, P, P, i64, i64, i64, ci, cd, ci, cd, ci, P, ctypes.POINTER(ci), P], ci),
+                "orc_rl_monitor_same": ([P, P, P, i64, i64, i64, i64, i64, i64, ci, cd, ci, cd, ci, P,
+                                         ctypes.POINTER(ci), P], ci),
                 "orc_accel_linear": ([i64, ci, P, P, P, P, P], ci),
                 "orc_psf_gaussian": ([i64, i64, i64, cd, cd, cd, P], ci),
                 "orc_psf_gaussian_grad": ([i64, i64, i64, cd, cd, cd, P, P], ci),
@@ -255,6 +257,20 @@ def rl_monitor(d, psf, max_iter: int, eps: float, metric: int, tol: float, check
     _check(_load().orc_rl_monitor(_p(dd), _p(p), None if rr is None else _p(rr), *dd.shape, int(max_iter),
                                   float(eps), int(metric), float(tol), int(check_every), _p(out), ctypes.byref(n),
                                   _p(hist)), "rl_monitor")
+    return out, int(n.value), hist[:n.value].copy()
+
+
+def rl_monitor_same(d, psf_box, max_iter: int, eps: float, metric: int, tol: float, check_every: int = 1,
+                    ref=None):
+    """rl_monitor with linear ("same"-mode) boundaries and a PSF box of any size."""
+    dd, p = _f64(d), _f64(psf_box)
+    rr = None if ref is None else _f64(ref)
+    out = np.empty_like(dd)
+    hist = np.zeros((max(1, int(max_iter)), 3), np.float64)
+    n = ctypes.c_int(0)
+    _check(_load().orc_rl_monitor_same(_p(dd), _p(p), None if rr is None else _p(rr), *dd.shape, *p.shape,
+                                       int(max_iter), float(eps), int(metric), float(tol), int(check_every), _p(out),
+                                       ctypes.byref(n), _p(hist)), "rl_monitor_same")
     return out, int(n.value), hist[:n.value].copy()
 
 

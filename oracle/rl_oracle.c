@@ -577,26 +577,25 @@ double orc_psnr_si(const double *x, const double *y, int64_t V)
  *   metric 0: delta_k < tol (relative change of the estimate);
  *   metric 1: k >= 1 and (NLL(u_{k-1}) - NLL(u_k)) / |NLL(u_k)| < tol;
  *   metric 2: k >= 1 and PSNR_k - PSNR_{k-1} < tol (decibels; needs ref).
- * out: the last estimate u_{n_done}. */
-int orc_rl_monitor(const double *d, const double *psf, const double *ref, int64_t nz, int64_t ny, int64_t nx,
-                   int max_iter, double eps, int metric, double tol, int check_every, double *out, int *n_done,
-                   double *hist)
+ * out: the last estimate u_{n_done}.
+ *
+ * monitor_run is that loop for any RL step: step(ctx, u, un, b) makes the next estimate
+ * un and leaves the forward blur b = h * u (before the clamp) for the likelihood. */
+typedef int (*monitor_step)(void *ctx, const double *u, double *un, double *b);
+
+static int monitor_run(monitor_step step, void *ctx, const double *d, const double *ref, int64_t V, int max_iter,
+                       double eps, int metric, double tol, int check_every, double *out, int *n_done, double *hist)
 {
-    if (!d || !psf || !out || !n_done || !hist || nz < 1 || ny < 1 || nx < 1 || max_iter < 1 ||
-        check_every < 1 || !(eps > 0) || metric < 0 || metric > 2 || (metric == 2 && !ref))
-        return -1;
-    int64_t V = nz * ny * nx;
-    double *Hs = malloc(sizeof(double) * 2 * (size_t)V);
     double *u = malloc(sizeof(double) * (size_t)V);
     double *un = malloc(sizeof(double) * (size_t)V);
     double *b = malloc(sizeof(double) * (size_t)V);
-    if (!Hs || !u || !un || !b) { free(Hs); free(u); free(un); free(b); return -2; }
-    int rc = orc_psf_spectrum(psf, Hs, nz, ny, nx);
+    if (!u || !un || !b) { free(u); free(un); free(b); return -2; }
+    int rc = 0;
     double u0 = orc_initial_value(d, V, eps);
     for (int64_t i = 0; i < V; ++i) u[i] = u0;
     int k = 0;
     while (!rc && k < max_iter) {
-        rc = orc_rl_iterate(Hs, d, u, eps, nz, ny, nx, un, b, NULL, NULL);
+        rc = step(ctx, u, un, b);
         if (rc) break;
         double num = 0.0, den = 0.0;
         for (int64_t i = 0; i < V; ++i) {
@@ -622,7 +621,82 @@ int orc_rl_monitor(const double *d, const double *psf, const double *ref, int64_
         memcpy(out, u, sizeof(double) * (size_t)V);
         *n_done = k;
     }
-    free(Hs); free(u); free(un); free(b);
+    free(u); free(un); free(b);
+    return rc;
+}
+
+struct circ_monitor {
+    const double *Hs, *d;
+    double eps;
+    int64_t nz, ny, nx;
+};
+
+static int circ_monitor_step(void *ctx, const double *u, double *un, double *b)
+{
+    const struct circ_monitor *c = ctx;
+    return orc_rl_iterate(c->Hs, c->d, u, c->eps, c->nz, c->ny, c->nx, un, b, NULL, NULL);
+}
+
+int orc_rl_monitor(const double *d, const double *psf, const double *ref, int64_t nz, int64_t ny, int64_t nx,
+                   int max_iter, double eps, int metric, double tol, int check_every, double *out, int *n_done,
+                   double *hist)
+{
+    if (!d || !psf || !out || !n_done || !hist || nz < 1 || ny < 1 || nx < 1 || max_iter < 1 ||
+        check_every < 1 || !(eps > 0) || metric < 0 || metric > 2 || (metric == 2 && !ref))
+        return -1;
+    int64_t V = nz * ny * nx;
+    double *Hs = malloc(sizeof(double) * 2 * (size_t)V);
+    if (!Hs) return -2;
+    int rc = orc_psf_spectrum(psf, Hs, nz, ny, nx);
+    struct circ_monitor c = {Hs, d, eps, nz, ny, nx};
+    if (!rc) rc = monitor_run(circ_monitor_step, &c, d, ref, V, max_iter, eps, metric, tol, check_every, out, n_done,
+                              hist);
+    free(Hs);
+    return rc;
+}
+
+/* The same monitored run with linear ("same"-mode) boundaries: the blur, the ratio, the
+ * adjoint and the update of orc_rl_same; every measure is taken over the image box. */
+struct same_monitor {
+    const struct same_geom *g;
+    const cplx *H;
+    cplx *work;
+    const double *d;
+    double *r, *q;
+    double eps;
+    int64_t V;
+};
+
+static int same_monitor_step(void *ctx, const double *u, double *un, double *b)
+{
+    const struct same_monitor *c = ctx;
+    int rc = same_filter(c->g, c->H, u, b, c->work, 0);                          /* forward conv */
+    if (rc) return rc;
+    for (int64_t i = 0; i < c->V; ++i) c->r[i] = c->d[i] / (b[i] > c->eps ? b[i] : c->eps);   /* ratio */
+    rc = same_filter(c->g, c->H, c->r, c->q, c->work, 1);                        /* adjoint */
+    if (rc) return rc;
+    for (int64_t i = 0; i < c->V; ++i) un[i] = u[i] * c->q[i];                   /* update */
+    return 0;
+}
+
+int orc_rl_monitor_same(const double *d, const double *psf, const double *ref, int64_t nz, int64_t ny, int64_t nx,
+                        int64_t kz, int64_t ky, int64_t kx, int max_iter, double eps, int metric, double tol,
+                        int check_every, double *out, int *n_done, double *hist)
+{
+    if (!d || !psf || !out || !n_done || !hist || nz < 1 || ny < 1 || nx < 1 || kz < 1 || ky < 1 || kx < 1 ||
+        max_iter < 1 || check_every < 1 || !(eps > 0) || metric < 0 || metric > 2 || (metric == 2 && !ref))
+        return -1;
+    const int64_t n[3] = {nz, ny, nx}, k[3] = {kz, ky, kx};
+    int64_t V = nz * ny * nx;
+    struct same_geom g;
+    cplx *H, *work;
+    int rc = same_setup(psf, n, k, &g, &H, &work);
+    double *r = malloc(sizeof(double) * (size_t)V), *q = malloc(sizeof(double) * (size_t)V);
+    if (!r || !q) rc = rc ? rc : -2;
+    struct same_monitor c = {&g, H, work, d, r, q, eps, V};
+    if (!rc) rc = monitor_run(same_monitor_step, &c, d, ref, V, max_iter, eps, metric, tol, check_every, out, n_done,
+                              hist);
+    free(H); free(work); free(r); free(q);
     return rc;
 }
 

@@ -1190,7 +1190,7 @@ static cubic_status_t time_best(cudaStream_t st, G &&prepare, F &&body, float *b
     cubic_status_t s = prepare();
     if (s == CUBIC_OK) s = body();
     float best = 1e30f;
-    for (int r = 0; r < 3 && s == CUBIC_OK; ++r) {
+    for (int r = 0; r < 5 && s == CUBIC_OK; ++r) {
         s = prepare();
         if (s != CUBIC_OK) break;
         cudaEventRecord(e0, st);
@@ -2057,6 +2057,25 @@ __global__ void __launch_bounds__(256) k_ref_sums(const float *__restrict__ x, c
         }
 }
 
+// Poisson likelihood sum (c - d ln c), c = max(b, eps), over the image columns of a
+// linear plan's padded rows (past them d = 0 and the term would count the blur that
+// spills into the padding); compensated, into the 64 (hi, lo) slots the ratio pass fills
+// for a circular plan.
+__global__ void __launch_bounds__(256) k_nll_image(const float *__restrict__ b, const float *__restrict__ d,
+                                                   int64_t rows, int64_t pitch, int64_t cols, float eps,
+                                                   float *__restrict__ slots)
+{
+    CFloat v{0.f, 0.f};
+    const int64_t n = rows * cols;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / cols, x = i - r * cols;
+        const float c = fmaxf(b[r * pitch + x], eps);
+        v = cf_add(v, c - d[r * pitch + x] * logf(c));
+    }
+    const int slot = (int)((blockIdx.x * 8 + (threadIdx.x >> 5)) & 63);
+    slot_add<256>(slots + 2 * slot, v);
+}
+
 // per-block (sum y, sum y^2) as (s, c) pairs, then min y and max y
 __global__ void __launch_bounds__(256) k_ref_moments(const float *__restrict__ y, int64_t V, float *__restrict__ part)
 {
@@ -2124,7 +2143,6 @@ extern "C" cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, cons
                                                       float *out, int *n_done, double *history, void *stream)
 {
     if (!plan || !image || !out || !n_done) return fail(CUBIC_ERR_INVALID_ARG, "plan, image, out, n_done must be non-null");
-    if (cubic_status_t g = no_linear(plan, "metric-guided stopping")) return g;
     if (max_iter < 1 || check_every < 1) return fail(CUBIC_ERR_INVALID_ARG, "max_iter and check_every must be >= 1");
     if (!(eps > 0.f) || !(eps < INFINITY)) return fail(CUBIC_ERR_INVALID_ARG, "eps must be finite and > 0");
     if (!(tol >= -INFINITY) || tol != tol) return fail(CUBIC_ERR_INVALID_ARG, "tol must not be NaN");
@@ -2141,7 +2159,9 @@ extern "C" cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, cons
     if (s != CUBIC_OK) return s;
     // [dslots: max_iter x 256][nslots: max_iter x 128][ref part: blocks x 6][ref moments: blocks x 6][rec: max_iter x 12]
     const size_t f_d = (size_t)max_iter * 256, f_n = (size_t)max_iter * 128, f_r = (size_t)kMonBlocks * 6;
-    const size_t f_rec = (size_t)max_iter * kMonRec, total = f_d + f_n + 2 * f_r + f_rec;
+    // a linear plan also keeps the ratio pass's b and r (padded rows) for the likelihood
+    const size_t f_lin = p->linear ? 2 * lin_elems(p) : 0;
+    const size_t f_rec = (size_t)max_iter * kMonRec, total = f_d + f_n + 2 * f_r + f_rec + f_lin;
     if (p->mon_cap < max_iter) {
         cudaDeviceSynchronize();
         cudaFree(p->mon);
@@ -2153,6 +2173,7 @@ extern "C" cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, cons
         p->mon_cap = max_iter;
     }
     float *dslots = p->mon, *nslots = dslots + f_d, *rpart = nslots + f_n, *mpart = rpart + f_r, *rec = mpart + f_r;
+    float *keep_b = rec + f_rec, *keep_r = keep_b + f_lin / 2;
     cudaStream_t st = (cudaStream_t)stream;
     CUBIC_CUDA(cudaMemsetAsync(p->mon, 0, (f_d + f_n) * sizeof(float), st));
 
@@ -2184,14 +2205,20 @@ extern "C" cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, cons
         return 20.0 * log10(range / sqrt(mse));
     };
 
-    if ((s = enqueue_init(p, image, eps, out, st)) != CUBIC_OK) return s;
+    // a linear plan iterates on its padded arrays: the padding adds zeros to the update's
+    // sums, the likelihood is summed over the image's columns by k_nll_image, and the PSNR
+    // is taken on the estimate cropped into out
+    float *uw = p->linear ? p->lin + lin_elems(p) : out;
+    const float *dw = p->linear ? p->lin : image;
+    s = p->linear ? lin_init(p, image, eps, p->lin, uw, st) : enqueue_init(p, image, eps, out, st);
+    if (s != CUBIC_OK) return s;
     XArgs xa = x_args(p);
     xa.spec_in = p->ws;
     xa.spec_out = p->ws;
-    xa.src = out;
-    xa.u = out;
-    xa.dst = out;
-    xa.d = image;
+    xa.src = uw;
+    xa.u = uw;
+    xa.dst = uw;
+    xa.d = dw;
     xa.eps = eps;
     CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
     std::vector<float> hrec;
@@ -2200,12 +2227,23 @@ extern "C" cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, cons
     while (k < max_iter) {
         if ((s = enqueue_yzy(p, p->ws, ZM_CONV, st)) != CUBIC_OK) return s;
         XArgs xr = xa;
-        xr.nll_stats = nslots + (size_t)k * 128;
+        if (p->linear) {
+            xr.keep_a = keep_b;
+            xr.keep_b = keep_r;
+        } else {
+            xr.nll_stats = nslots + (size_t)k * 128;
+        }
         CUBIC_CUDA(run_x(p, XM_RATIO, xr, st));
+        if (p->linear) {
+            k_nll_image<<<kMonBlocks, 256, 0, st>>>(keep_b, dw, p->iz * p->iy, p->nx, p->ix, eps,
+                                                     nslots + (size_t)k * 128);
+            CUBIC_CUDA(cudaGetLastError());
+        }
         if ((s = enqueue_yzy(p, p->ws, ZM_CORR, st)) != CUBIC_OK) return s;
         XArgs xu = xa;
         xu.stats = dslots + (size_t)k * 256;
         CUBIC_CUDA(run_x(p, k + 1 < max_iter ? XM_UPDATE : XM_FINAL, xu, st));
+        if (p->linear && (reference || k + 1 == max_iter) && (s = lin_crop(p, uw, out, st)) != CUBIC_OK) return s;
         if (reference) k_ref_sums<<<kMonBlocks, 256, 0, st>>>(out, reference, p->V, rpart);
         k_metrics<<<1, 32, 0, st>>>(dslots + (size_t)k * 256, nslots + (size_t)k * 128, reference ? rpart : nullptr,
                                     kMonBlocks, rec + (size_t)k * kMonRec);
@@ -2228,9 +2266,11 @@ extern "C" cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, cons
             if (metric == CUBIC_METRIC_REL_CHANGE) stop = h[0] < tol;
             else if (k >= 2 && metric == CUBIC_METRIC_NLL) stop = (h[-2] - h[1]) / fabs(h[1]) < tol;
             else if (k >= 2 && metric == CUBIC_METRIC_PSNR) stop = h[2] - h[-1] < tol;
-            if (stop) break;  // out holds u_k (the update wrote it)
+            if (stop) break;  // the estimate holds u_k (the update wrote it)
         }
     }
+    // a linear plan without a reference crops only after the last iteration it ran
+    if (p->linear && !reference && k < max_iter && (s = lin_crop(p, uw, out, st)) != CUBIC_OK) return s;
     *n_done = k;
     if (history) std::copy(hist.begin(), hist.begin() + 3 * (size_t)k, history);
     return CUBIC_OK;

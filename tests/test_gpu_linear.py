@@ -150,13 +150,45 @@ def test_linear_automatic_stopping(cr):
     assert rel_l2(out.cpu().numpy(), oracle.rl_same(d, psf, n_stop, 1e-6)) <= 1e-4
 
 
+@pytest.mark.parametrize("n,k", [((24, 40, 48), (7, 9, 9)), ((9, 15, 30), (5, 5, 3))])
+def test_linear_monitor_matches_oracle(cr, n, k):
+    # the likelihood counts the image's voxels only (not the blur in the padding), the
+    # PSNR is taken on the cropped estimate; thresholds midway between two gains stop both
+    # sides at the same iteration
+    d, xt = synth.make_volume(n, 3, (1.5, 3.0), 10.0, 1.5, 3.0, 61 + sum(n))
+    psf = gaussian_box(k, 1.3, 2.2)
+    ref_out, _, h_ref = oracle.rl_monitor_same(d, psf, 12, 1e-6, oracle.METRIC_REL_CHANGE, 0.0, 1, xt)
+    plan = cr.cubic_rl_plan_linear(n, dev(psf))
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    dd, rr = dev(d), dev(xt)
+    n_done, hist = cr.cubic_rl_deconvolve_monitor(plan, dd, 12, 1e-6, cr.METRIC_REL_CHANGE, 0.0, 1, out, rr)
+    h = np.array(hist)
+    assert n_done == 12
+    assert np.allclose(h[:, 0], h_ref[:, 0], rtol=1e-3)
+    assert np.allclose(h[:, 1], h_ref[:, 1], rtol=1e-6, atol=0)
+    assert np.allclose(h[:, 2], h_ref[:, 2], atol=1e-3)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), ref_out) <= 1e-4
+    gain = (h_ref[:-1, 1] - h_ref[1:, 1]) / np.abs(h_ref[1:, 1])
+    tol = 0.5 * (gain[4] + gain[5])
+    n_nll, _ = cr.cubic_rl_deconvolve_monitor(plan, dd, 12, 1e-6, cr.METRIC_NLL, tol, 1, out)
+    _, n_ref, _ = oracle.rl_monitor_same(d, psf, 12, 1e-6, oracle.METRIC_NLL, tol, 1)
+    assert n_nll == n_ref
+    torch.cuda.synchronize()        # without a reference, out is cropped once at the stop
+    assert rel_l2(out.cpu().numpy(), oracle.rl_same(d, psf, n_nll, 1e-6)) <= 1e-4
+    dpsnr = h_ref[1:, 2] - h_ref[:-1, 2]
+    tol = 0.5 * (dpsnr[3] + dpsnr[4])
+    n_psnr, _ = cr.cubic_rl_deconvolve_monitor(plan, dd, 12, 1e-6, cr.METRIC_PSNR, tol, 2, out, rr)
+    _, n_ref, _ = oracle.rl_monitor_same(d, psf, 12, 1e-6, oracle.METRIC_PSNR, tol, 2, xt)
+    assert n_psnr == n_ref
+
+
 def test_linear_plan_errors(cr):
     n, k = (8, 10, 12), (3, 3, 3)
     plan = cr.cubic_rl_plan_linear(n, dev(np.ones(k, np.float32)))
     img = dev(np.ones(n, np.float32))
     out = torch.empty_like(img)
-    for call in (lambda: cr.cubic_rl_deconvolve_monitor(plan, img, 3, 1e-6, cr.METRIC_NLL, 0.0, 1, out),
-                 lambda: cr.cubic_rl_deconvolve_ckpt(plan, img, 3, 1e-6, 1, torch.empty((3,) + n, device="cuda"), out),
+    for call in (lambda: cr.cubic_rl_deconvolve_ckpt(plan, img, 3, 1e-6, 1, torch.empty((3,) + n, device="cuda"), out),
                  lambda: cr.cubic_fsc(plan, img, out, 4)):
         with pytest.raises(cr.CubicError) as e:
             call()

@@ -774,6 +774,50 @@ def test_rl_accel_same_composition():
     assert np.all((a >= 0) & (a <= 1)) and a[2:].max() > 0.3
 
 
+def test_rl_monitor_same_against_direct_loops():
+    # every measure of the linear-boundary monitor from the direct loops: delta_k, the
+    # likelihood of u_k from its same-mode blur over the image box, the PSNR of u_{k+1}
+    shape, k = (4, 5, 6), (3, 5, 3)
+    r = np.random.default_rng(96)
+    d = r.uniform(1, 20, shape)
+    ref = r.uniform(0, 10, shape)
+    psf = r.uniform(0.1, 1, k)
+    psf /= psf.sum()
+    eps = 1e-6
+    u = np.full(shape, d.mean())
+    rows = []
+    for _ in range(5):
+        b = direct_same(psf, u)
+        c = np.maximum(b, eps)
+        un = u * direct_same(psf, d / c, True)
+        rows.append((np.linalg.norm(un - u) / np.linalg.norm(u), np.sum(c - d * np.log(c)),
+                     oracle.psnr_si(un, ref)))
+        u = un
+    out, n, h = oracle.rl_monitor_same(d, psf, 5, eps, oracle.METRIC_REL_CHANGE, 0.0, 1, ref)
+    assert n == 5 and np.allclose(out, u, rtol=1e-11)
+    assert np.allclose(h, np.array(rows), rtol=1e-10, atol=0)
+    # the stop rules read the same history as the circular monitor: stop at the first check
+    # whose likelihood gain falls under tol
+    gain = (h[:-1, 1] - h[1:, 1]) / np.abs(h[1:, 1])
+    tol = 0.5 * (gain[1] + gain[2])
+    _, n, _ = oracle.rl_monitor_same(d, psf, 5, eps, oracle.METRIC_NLL, tol, 1, ref)
+    assert n == 4 and np.allclose(oracle.rl_monitor_same(d, psf, n, eps, 0, 0.0, 1)[0], oracle.rl_same(d, psf, n, eps),
+                                  rtol=1e-13, atol=0)
+
+
+def test_rl_monitor_same_one_voxel_psf_closed_form():
+    # a 1-voxel PSF: b = u, so u_1 = d and every later step leaves it there
+    d = np.random.default_rng(99).uniform(1, 20, (3, 4, 5))
+    u0 = d.mean()
+    _, n, h = oracle.rl_monitor_same(d, np.ones((1, 1, 1)), 3, 1e-6, oracle.METRIC_REL_CHANGE, -1.0, 1)
+    assert n == 3
+    assert np.isclose(h[0, 0], np.linalg.norm(d - u0) / (u0 * np.sqrt(d.size)), rtol=1e-12)
+    assert np.isclose(h[0, 1], np.sum(u0 - d * np.log(u0)), rtol=1e-12)
+    assert np.allclose(h[1:, 0], 0.0, atol=1e-15)
+    assert np.allclose(h[1:, 1], np.sum(d - d * np.log(d)), rtol=1e-12)
+    assert np.all(np.isnan(h[:, 2]))
+
+
 # ------------------------------------------------------------ single-image FSC
 
 def test_fsc_split_block_constant_and_checkerboard():
