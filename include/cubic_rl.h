@@ -76,19 +76,27 @@ CUBIC_API int cubic_rl_supported_length(int64_t n);
 CUBIC_API cubic_status_t cubic_rl_plan(cubic_rl_plan_t *plan, const int64_t dims[3], const float *psf,
                              unsigned flags, void *stream);
 
-/* Replace the PSF of an existing plan (same dims) -- e.g. after a PSF-parameter step. */
+/* Replace the PSF of an existing plan -- e.g. after a PSF-parameter step.  psf: device
+ * float32 of the plan's PSF dims (the image dims, or psf_dims for a cubic_rl_plan_linear
+ * plan), peak at floor(n/2), 16-byte aligned; the caller keeps owning it.  H is rebuilt on
+ * `stream` and the point-symmetry check that selects the real-spectrum Z pass is redone
+ * (one stream synchronisation).  Errors: INVALID_ARG (null pointers), ALIGNMENT,
+ * OUT_OF_MEMORY, CUDA. */
 CUBIC_API cubic_status_t cubic_rl_plan_update_psf(cubic_rl_plan_t plan, const float *psf, void *stream);
 
-/* Release a plan and everything it allocated (synchronises the device first). */
+/* Release a plan and everything it allocated (synchronises the device first; a workspace
+ * given by cubic_rl_set_workspace stays the caller's).  NULL is accepted and ignored. */
 CUBIC_API cubic_status_t cubic_rl_plan_destroy(cubic_rl_plan_t plan);
 
 /* Bytes of device scratch one deconvolution call of this plan needs (the complex
- * half-spectrum work array). */
+ * half-spectrum work array).  Errors: INVALID_ARG (null pointers). */
 CUBIC_API cubic_status_t cubic_rl_workspace_bytes(cubic_rl_plan_t plan, size_t *bytes);
 
 /* Give the plan caller-owned device scratch of at least cubic_rl_workspace_bytes()
- * bytes (256-byte aligned).  Without it the plan allocates its own on first use.
- * The caller must keep the memory alive while the plan uses it. */
+ * bytes (256-byte aligned).  Without it the plan allocates its own on first use; a
+ * workspace the plan allocated before is freed (after a device synchronisation).
+ * The caller must keep the memory alive while the plan uses it.  Errors: INVALID_ARG
+ * (null pointers, too small), ALIGNMENT. */
 CUBIC_API cubic_status_t cubic_rl_set_workspace(cubic_rl_plan_t plan, void *dev_ptr, size_t bytes);
 
 /* Richardson-Lucy deconvolution, Section 4 of the paper: n_iter iterations of
