@@ -2173,7 +2173,7 @@ extern "C" cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, cons
         p->mon_cap = max_iter;
     }
     float *dslots = p->mon, *nslots = dslots + f_d, *rpart = nslots + f_n, *mpart = rpart + f_r, *rec = mpart + f_r;
-    float *keep_b = rec + f_rec, *keep_r = keep_b + f_lin / 2;
+    float *kept_b = rec + f_rec, *kept_r = kept_b + f_lin / 2;
     cudaStream_t st = (cudaStream_t)stream;
     CUBIC_CUDA(cudaMemsetAsync(p->mon, 0, (f_d + f_n) * sizeof(float), st));
 
@@ -2228,14 +2228,14 @@ extern "C" cubic_status_t cubic_rl_deconvolve_monitor(cubic_rl_plan_t plan, cons
         if ((s = enqueue_yzy(p, p->ws, ZM_CONV, st)) != CUBIC_OK) return s;
         XArgs xr = xa;
         if (p->linear) {
-            xr.keep_a = keep_b;
-            xr.keep_b = keep_r;
+            xr.keep_a = kept_b;
+            xr.keep_b = kept_r;
         } else {
             xr.nll_stats = nslots + (size_t)k * 128;
         }
         CUBIC_CUDA(run_x(p, XM_RATIO, xr, st));
         if (p->linear) {
-            k_nll_image<<<kMonBlocks, 256, 0, st>>>(keep_b, dw, p->iz * p->iy, p->nx, p->ix, eps,
+            k_nll_image<<<kMonBlocks, 256, 0, st>>>(kept_b, dw, p->iz * p->iy, p->nx, p->ix, eps,
                                                      nslots + (size_t)k * 128);
             CUBIC_CUDA(cudaGetLastError());
         }
