@@ -242,17 +242,19 @@ def run_ours(args, w: synth.Workload):
     value = job_rate(V * n_iter * args.steps, world, ms)
     e2e = job_rate(V * n_iter * args.steps, world, ms_e2e)
 
-    # roofline of the kernel with the largest share of device time
+    # roofline of the kernel instance with the largest share of device time
     kernels = {k: v for k, v in prof.items() if v["timed"] > 0}
-    top = max(kernels, key=lambda k: kernels[k]["ms"])
-    tk = kernels[top]
+    top, members, tk = top_instance(kernels)
     per_launch_bytes = tk["bytes"] / tk["launches"]
     avg_s = tk["ms"] / tk["timed"] * 1e-3
     peak, peak_src = hbm_peak()
     achieved = per_launch_bytes / avg_s / 1e9
     total_kernel_ms = sum(v["ms"] for v in kernels.values())
     launches = sum(v["launches"] for v in prof.values())
-    traffic = load_traffic(top, w)
+    traffic = load_traffic(members, w)
+    # algorithmic bytes per voxel-iteration of the kernels that ran (80 with a real PSF
+    # spectrum, 84 with a complex one), from the library's per-launch byte counts
+    bpvi = sum(v["bytes"] for v in kernels.values()) / (V * n_iter * args.steps)
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -267,8 +269,10 @@ def run_ours(args, w: synth.Workload):
         "roofline": {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "peak_source": peak_src,
-                     "bytes_per_launch": per_launch_bytes},
-        "model_84B_frac": round(value * 84.0 / peak, 4),
+                     "bytes_per_launch": per_launch_bytes, "share": round(tk["ms"] / sum(
+                         v["ms"] for v in kernels.values()), 4)},
+        "model": {"bytes_per_voxel_iter": round(bpvi, 2), "frac": round(value * bpvi / peak, 4),
+                  "note": "whole-step algorithmic bytes at the measured copy bandwidth"},
         "kernels": {k: {"share": round(v["ms"] / total_kernel_ms, 4),
                         "avg_us": round(v["ms"] / v["timed"] * 1e3, 2),
                         "GBps": round(v["bytes"] / v["launches"] / (v["ms"] / v["timed"] * 1e-3) / 1e9, 1)}
@@ -283,16 +287,97 @@ def run_ours(args, w: synth.Workload):
     if not args.no_metrics:
         result["metrics"] = run_metrics(cr, args, plan, d, w, ms / args.steps / n_iter)
     if not args.no_paper_shape:
-        result["paper_shape"] = run_paper_shape(cr, args)
+        result["paper_shape"] = run_paper_shape(cr, args, keep_case=(rank == 0 and world == 1 and
+                                                                     not args.no_accuracy))
     if not args.no_batched:
         result["batched"] = run_batched(cr, args, ranks)
     if not args.no_grad:
         result["fwd_bwd"] = run_fwd_bwd(cr, args)
+    if not args.no_configs:
+        result["configs"] = run_small_configs(cr, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, d_host, args.cpu_sample)
-        result["accuracy"] = accuracy(cr, plan, d, d_host, w)
+    if rank == 0 and world == 1 and not args.no_accuracy:
+        result["accuracy"] = accuracy(cr, plan, d, d_host, w, result.get("configs"))
+    _small_plans.clear()
+    _paper_case.clear()
     ranks.close()
     return rank, result
+
+
+# the same kernel instance serves these pass kinds (same launch shape, a runtime mode)
+INSTANCES = {"y_fwd": "y", "y_inv": "y", "z_conv": "z", "z_corr": "z"}
+
+
+def top_instance(kernels):
+    """(name, member kinds, summed profile) of the kernel instance with the most device time."""
+    groups = {}
+    for k, v in kernels.items():
+        groups.setdefault(INSTANCES.get(k, k), []).append(k)
+    def total(ks, f):
+        return sum(kernels[k][f] for k in ks)
+    name = max(groups, key=lambda g: total(groups[g], "ms"))
+    ks = sorted(groups[name])
+    tk = {f: total(ks, f) for f in ("ms", "timed", "launches", "bytes")}
+    label = name if ks == [name] else f"{name} ({' + '.join(ks)}: one kernel instance)"
+    return label, ks, tk
+
+
+def run_small_configs(cr, args):
+    """The two smaller plain workloads, each in its own tuned launch configuration: 64x64x32
+    (20 iterations; launch-latency bound, so also replayed as a captured CUDA graph) and
+    256x256x128 (100 iterations; its 176 MB working set sits mostly in the 129 MB L2)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for wl, reps in ((synth.SMALL, 50), (synth.MEDIUM, 5)):
+        dh, _ = synth.workload_volume(wl)
+        img = torch.from_numpy(dh).cuda()
+        psf = torch.empty(wl.shape, dtype=torch.float32, device="cuda")
+        cr.cubic_psf_gaussian(wl.shape, wl.psf_sigma_xy, wl.psf_sigma_z, 1.0, psf)
+        plan = cr.cubic_rl_plan(wl.shape, psf)
+        out = torch.empty_like(img)
+        cr.cubic_rl_autotune(plan, img, out)
+        n = wl.n_iter
+
+        def call():
+            cr.cubic_rl_deconvolve(plan, img, n, 1e-6, out)
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        ms = timed(call)
+        r = {"n_iter": n, "ms": round(ms, 4), "us_per_iter": round(ms * 1e3 / n, 2),
+             "value": round(wl.voxels * n / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
+             "variants_xyz": list(cr.cubic_rl_plan_variants(plan)[1])}
+        if wl is synth.SMALL:
+            # the same call captured once into a CUDA graph and replayed
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(stream)
+            with torch.cuda.stream(side):
+                call()
+                with torch.cuda.graph(g, stream=side):
+                    call()
+            stream.wait_stream(side)
+            ms_g = timed(g.replay)
+            r["graph"] = {"ms": round(ms_g, 4), "us_per_iter": round(ms_g * 1e3 / n, 2),
+                          "value": round(wl.voxels * n / (ms_g * 1e-3) / 1e9, 3)}
+        res[wl.name] = r
+        _small_plans[wl.name] = (plan, img, dh, psf)
+    return res
+
+
+_small_plans = {}   # workload name -> (plan, image on the device, image on the host, PSF)
 
 
 def run_batched(cr, args, ranks=None):
@@ -447,7 +532,10 @@ def run_metrics(cr, args, plan, d, w: synth.Workload, plain_ms_per_iter: float):
                     "first_shell_below_1_7": int(below[0]) if below.size else None}}
 
 
-def run_paper_shape(cr, args):
+_paper_case = {}   # "case": (GPU estimate, image, PSF, iterations) of the paper-shaped volume
+
+
+def run_paper_shape(cr, args, keep_case: bool = False):
     """The paper's stack shape, ZYX 30 x 2160 x 2560 with a PSF of the same size (circular FFT
     convolution), 50 iterations: Gvoxel-iter/s and the top kernel's HBM fraction."""
     import torch
@@ -460,6 +548,7 @@ def run_paper_shape(cr, args):
     psf = torch.empty(shape, dtype=torch.float32, device="cuda")
     cr.cubic_psf_gaussian(shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0, psf)
     plan = cr.cubic_rl_plan(shape, psf)
+    psf_host = psf.cpu().numpy() if keep_case else None
     del psf
     out = torch.empty_like(d)
     cr.cubic_rl_autotune(plan, d, out)
@@ -479,6 +568,7 @@ def run_paper_shape(cr, args):
     cr.cubic_rl_profile(plan, False)
     kernels = {k: v for k, v in prof.items() if v["timed"] > 0}
     total = sum(v["ms"] for v in kernels.values())
+    bpvi = sum(v["bytes"] for v in kernels.values()) / (V * n_iter * reps)
     peak, _ = hbm_peak()
     per = {k: {"share": round(v["ms"] / total, 4), "avg_us": round(v["ms"] / v["timed"] * 1e3, 2),
                "frac": round(v["bytes"] / v["launches"] / (v["ms"] / v["timed"] * 1e-3) / 1e9 / peak, 4)}
@@ -486,6 +576,12 @@ def run_paper_shape(cr, args):
     value = V * n_iter / (ms * 1e-3) / 1e9
     flux = abs(out.double().sum().item() / d.double().sum().item() - 1.0)
     variants = list(cr.cubic_rl_plan_variants(plan)[1])
+    if keep_case:
+        # for the accuracy leg: a short run of the timed plan, compared with the oracle later
+        n_acc = 2
+        cr.cubic_rl_deconvolve(plan, d, n_acc, eps, out)
+        torch.cuda.synchronize()
+        _paper_case["case"] = (out.cpu().numpy(), d.cpu().numpy(), psf_host, n_acc)
     del plan
 
     # linear (zero-padded, same-mode) boundaries with a 31 x 33 x 33 PSF box, same data
@@ -511,7 +607,7 @@ def run_paper_shape(cr, args):
                         f"(sigma {w.psf_sigma_xy}, {w.psf_sigma_z}), {n_iter} iterations, Poisson data generated "
                         "on the device",
             "value": round(value, 3), "unit": UNIT, "ms": round(ms, 3),
-            "model_84B_frac": round(value * 84.0 / peak, 4),
+            "model": {"bytes_per_voxel_iter": round(bpvi, 2), "frac": round(value * bpvi / peak, 4)},
             "variants_xyz": variants,
             "flux_rel_err": flux,
             "kernels": per,
@@ -586,19 +682,23 @@ def run_fwd_bwd(cr, args):
             "value": round(vox * n_iter / (ms_fb * 1e-3) / 1e9, 3), "unit": "Gvoxel-iter/s (fwd+bwd)"}
 
 
-def load_traffic(kernel: str, w: synth.Workload):
-    """DRAM bytes per launch from the committed ncu summary, if it covers this kernel build."""
+def load_traffic(kinds, w: synth.Workload):
+    """DRAM bytes per launch of a kernel instance (the mean over the pass kinds it serves)
+    from the committed ncu summary, if it covers this kernel build."""
     path = os.path.join(ROOT, "profiles", "ncu_dram_traffic.txt")
     if not os.path.exists(path):
         return None
     src_hash = source_hash()
+    found = {}
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[1] == w.name:
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] in kinds and parts[1] == w.name:
             if parts[3] != src_hash:
                 return None
-            return float(parts[2])
-    return None
+            found[parts[0]] = float(parts[2])
+    if set(found) != set(kinds):
+        return None
+    return sum(found.values()) / len(found)
 
 
 def source_hash() -> str:
@@ -645,32 +745,90 @@ def cpu_baseline(w: synth.Workload, d_host, sample: str, iters: int = 1):
                       f"{dt:.1f} s"}
 
 
-def accuracy(cr, plan, d, d_host, w: synth.Workload):
-    """Relative L2 error of the float32 GPU estimate against the FP64 oracle, per workload:
-    the small one at its 20 iterations (the gated tolerance is 1e-4), 256x256x128 at 10 and
-    the timed volume in its benchmarked launch configuration at 2 (reported, not gated)."""
+def err_stats(got, ref):
+    """rel_l2 = ||got - ref|| / ||ref||; max_rel = max |got - ref| / max |ref| (the worst voxel
+    against the volume's scale)."""
+    got = np.asarray(got, np.float64)
+    diff = got - ref
+    return {"rel_l2": float(np.linalg.norm(diff) / np.linalg.norm(ref)),
+            "max_rel": float(np.max(np.abs(diff)) / np.max(np.abs(ref)))}
+
+
+def accuracy(cr, plan, d, d_host, w: synth.Workload, configs=None):
+    """Error of the float32 GPU estimate against the FP64 oracle on the same inputs and PSF,
+    for every workload at its stated iteration count: 64x64x32 at 20, 256x256x128 at 100, the
+    timed volume (1024x1024x128) at its 50 in its benchmarked launch configuration.  Two stated
+    subsets, where the oracle's Bluestein transforms of the non-power-of-two lengths are too
+    slow for a bench run: the paper-shaped volume at 2 iterations, and 8 of the 64 batched
+    volumes (every eighth, from the fifth) at their 50.  Each entry gives rel_l2, max_rel, the
+    oracle's wall time on the host cores and, for the first two, the oracle's rate next to the
+    GPU's."""
     import torch
     import oracle
 
-    def err(plan_, img, img_host, psf_host, n):
+    def run(plan_, img, n):
         out = torch.empty_like(img)
         cr.cubic_rl_deconvolve(plan_, img, n, 1e-6, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    def with_oracle(got, img_host, psf_host, n):
+        t0 = time.perf_counter()
         ref = oracle.rl(img_host, psf_host, n, 1e-6)
-        diff = out.cpu().numpy().astype(np.float64) - ref
-        return float(np.linalg.norm(diff) / np.linalg.norm(ref))
+        dt = time.perf_counter() - t0
+        r = {"n_iter": n, **err_stats(got, ref), "oracle_s": round(dt, 1)}
+        r["oracle_rate"] = round(img_host.size * n / dt / 1e9, 6)
+        return r
 
     res = {}
-    for wl, n in ((synth.SMALL, synth.SMALL.n_iter), (synth.MEDIUM, 10)):
-        dh, _ = synth.workload_volume(wl)
-        psf = torch.empty(wl.shape, dtype=torch.float32, device="cuda")
-        cr.cubic_psf_gaussian(wl.shape, wl.psf_sigma_xy, wl.psf_sigma_z, 1.0, psf)
-        p = cr.cubic_rl_plan(wl.shape, psf)
-        res[wl.name] = {"n_iter": n, "rel_l2": err(p, torch.from_numpy(dh).cuda(), dh, psf.cpu().numpy(), n)}
+    for wl in (synth.SMALL, synth.MEDIUM):
+        if wl.name in _small_plans:
+            p, img, dh, psf = _small_plans[wl.name]
+        else:
+            dh, _ = synth.workload_volume(wl)
+            img = torch.from_numpy(dh).cuda()
+            psf = torch.empty(wl.shape, dtype=torch.float32, device="cuda")
+            cr.cubic_psf_gaussian(wl.shape, wl.psf_sigma_xy, wl.psf_sigma_z, 1.0, psf)
+            p = cr.cubic_rl_plan(wl.shape, psf)
+        r = with_oracle(run(p, img, wl.n_iter), dh, psf.cpu().numpy(), wl.n_iter)
+        if configs and wl.name in configs:
+            r["gpu_rate"] = configs[wl.name]["value"]
+        res[wl.name] = r
     psf = torch.empty(w.shape, dtype=torch.float32, device="cuda")
     cr.cubic_psf_gaussian(w.shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0, psf)
-    res[w.name] = {"n_iter": 2, "rel_l2": err(plan, d, d_host, psf.cpu().numpy(), 2),
-                   "launch_shapes_xyz": list(cr.cubic_rl_plan_variants(plan)[1])}
-    res["reference"] = "FP64 CPU oracle, same inputs and PSF"
+    res[w.name] = with_oracle(run(plan, d, w.n_iter), d_host, psf.cpu().numpy(), w.n_iter)
+    res[w.name]["launch_shapes_xyz"] = list(cr.cubic_rl_plan_variants(plan)[1])
+    del psf
+    if _paper_case:
+        got, dh, psf_h, n = _paper_case["case"]
+        res[synth.PAPER.name] = with_oracle(got, dh, psf_h, n)
+        res[synth.PAPER.name]["subset"] = f"{n} of {synth.PAPER.n_iter} iterations"
+    # batched workload: one batched call over the subset, each volume against the oracle
+    all_shapes = synth.batch_shapes()
+    picks = list(range(4, len(all_shapes), 8))
+    plans, imgs, hosts = [], [], []
+    for j in picks:
+        shape = all_shapes[j]
+        dh, _ = synth.batch_volume(j, shape)
+        bpsf = torch.empty(shape, dtype=torch.float32, device="cuda")
+        cr.cubic_psf_gaussian(shape, synth.SMALL.psf_sigma_xy, synth.SMALL.psf_sigma_z, 1.0, bpsf)
+        plans.append(cr.cubic_rl_plan(shape, bpsf))
+        imgs.append(torch.from_numpy(dh).cuda())
+        hosts.append((dh, bpsf.cpu().numpy()))
+    outs = [torch.empty_like(i) for i in imgs]
+    cr.cubic_rl_deconvolve_batched(plans, imgs, synth.BATCH_ITERS, 1e-6, outs)
+    torch.cuda.synchronize()
+    per = []
+    t_or = 0.0
+    for j, (dh, bpsf), out in zip(picks, hosts, outs):
+        t0 = time.perf_counter()
+        ref = oracle.rl(dh, bpsf, synth.BATCH_ITERS, 1e-6)
+        t_or += time.perf_counter() - t0
+        per.append({"volume": j, "zyx": list(dh.shape), **err_stats(out.cpu().numpy(), ref)})
+    res["batched"] = {"n_iter": synth.BATCH_ITERS, "subset": f"volumes {picks} of {len(all_shapes)}",
+                      "rel_l2": max(v["rel_l2"] for v in per), "max_rel": max(v["max_rel"] for v in per),
+                      "oracle_s": round(t_or, 1), "per_volume": per}
+    res["reference"] = "FP64 CPU oracle, same inputs and PSF; rel_l2 and max_rel of the batched entry are the worst volume's"
     return res
 
 
@@ -734,6 +892,9 @@ def main():
     ap.add_argument("--no-accel", action="store_true", help="skip the accelerated-RL leg")
     ap.add_argument("--no-paper-shape", action="store_true", help="skip the 2560x2160x30 leg")
     ap.add_argument("--no-metrics", action="store_true", help="skip the stopping-metric and FSC leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip timing the 64x64x32 and 256x256x128 workloads")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the comparison with the FP64 oracle at the stated iteration counts (minutes of CPU)")
     ap.add_argument("--ncu-target", metavar="VX,VY,VZ",
                     help="profiling target only: plan + --ncu-iters RL iterations with these launch shapes")
     ap.add_argument("--ncu-iters", type=int, default=1)

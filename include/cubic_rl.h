@@ -173,6 +173,23 @@ CUBIC_API cubic_status_t cubic_psf_gaussian(const int64_t dims[3], float sigma_x
  * stores, so their outputs are then undefined. */
 CUBIC_API cubic_status_t cubic_rl_stream_status(cubic_rl_plan_t plan, void *stream);
 
+/* Limit, in nanoseconds of the GPU's global timer, of every bounded device wait made by
+ * the plan's kernels (the waits on the asynchronous tile copies).  0 restores the default
+ * of 2 s.  A wait that reaches the limit gives up as described for cubic_rl_stream_status.
+ * Errors: INVALID_ARG for a null plan. */
+CUBIC_API cubic_status_t cubic_rl_plan_set_wait_limit(cubic_rl_plan_t plan, uint64_t limit_ns);
+
+/* Test support for the failure path of the bounded waits (no counterpart in the paper).
+ * Arms a one-shot setting for the whole process: the next Y-pass launch that uses a
+ * TMA-pipelined launch shape -- on any plan, or inside cubic_rl_deconvolve_noalloc -- waits
+ * at most wait_ns per tile, and its first CTA does not issue the copy of its first tile.
+ * That CTA's wait then runs out: it sets the device error word, waits for the copies it
+ * did issue and returns, so no copy is left in flight and the context stays usable.  The
+ * call that made the launch reports CUBIC_ERR_TIMEOUT through cubic_rl_stream_status (or
+ * cubic_rl_noalloc_status) and its result is wrong by design.  wait_ns == 0 disarms a
+ * setting that no launch has taken yet.  Always CUBIC_OK. */
+CUBIC_API cubic_status_t cubic_test_skip_next_tile_copy(uint64_t wait_ns);
+
 /* ---- launch shapes and autotuning ---- */
 
 /* counts[3] = number of compiled launch-shape variants of the X, Y and Z passes for this
@@ -200,22 +217,35 @@ CUBIC_API cubic_status_t cubic_rl_autotune(cubic_rl_plan_t plan, const float *im
                                            void *stream);
 
 /* Allocation-free deconvolution.  The paper has no counterpart: this is a service for
- * callers that must not allocate device memory -- code running while another framework
- * captures the stream into a CUDA graph, processes whose device memory is fully reserved
- * by a pool allocator, and latency-critical code that cannot take cudaMalloc's implicit
- * device synchronisation.  Same result as cubic_rl_plan + cubic_rl_deconvolve on
- * (psf, image), but every internal buffer lives in one fixed 8 MiB device array that each
- * GPU loading this library holds until the process exits; nothing is allocated or freed.
+ * callers that cannot call cudaMalloc -- a framework whose device memory is fully
+ * reserved by its own pool allocator, plug-in code whose host application does not let it
+ * allocate, and latency-critical loops that cannot take cudaMalloc's implicit device-wide
+ * synchronisation.  It computes what cubic_rl_plan + cubic_rl_deconvolve compute on
+ * (psf, image), equal to float32 rounding: it always multiplies by the complex PSF
+ * spectrum, because finding that a PSF is point-symmetric (which lets a plan use the
+ * cheaper real spectrum) takes a host synchronisation.  Every internal buffer lives in one
+ * fixed 8 MiB device array that each GPU loading this library holds until the process
+ * exits; nothing is allocated or freed.
  * Limit: nz * ny * xp <= about 2^19 complex elements, xp = nx/2+1 rounded up to 16 (e.g.
- * 64x64x64); larger volumes get CUBIC_ERR_UNSUPPORTED_SIZE with the byte counts.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress),
- * so make that first call outside any stream capture.  All calls share the array: calls
- * whose work overlaps on the GPU (other streams, other host threads) race and give wrong
- * results; serialise them.  psf, image, out: device float32 [nz][ny][nx], 16-byte
- * aligned; out must not overlap image. */
+ * 64x64x64 or 80x80x128); larger volumes get CUBIC_ERR_UNSUPPORTED_SIZE with the byte
+ * counts.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make that first
+ * call before any stream capture; the kept address does not survive a cudaDeviceReset.
+ * All calls share the array, which keeps the last call's contents: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and give wrong results;
+ * serialise them.  A bounded device wait that runs out sets an error word in the array
+ * that stays set until cubic_rl_noalloc_status reads it.  psf, image, out: device float32
+ * [nz][ny][nx], 16-byte aligned; out must not overlap image.  Errors: INVALID_ARG,
+ * UNSUPPORTED_SIZE, ALIGNMENT, CUDA. */
 CUBIC_API cubic_status_t cubic_rl_deconvolve_noalloc(const int64_t dims[3], const float *psf,
                                                      const float *image, int n_iter, float eps,
                                                      float *out, void *stream);
+
+/* Device-side status of the allocation-free calls on the current device: synchronises
+ * `stream`, then returns CUBIC_ERR_TIMEOUT (and clears the word) if a bounded device wait
+ * of any allocation-free call gave up since the last check, else CUBIC_OK.  Allocates
+ * nothing.  The paper has no counterpart. */
+CUBIC_API cubic_status_t cubic_rl_noalloc_status(void *stream);
 
 /* Richardson-Lucy with metric-guided stopping.  The paper (Section 4) selects the
  * iteration count by monitoring an image-quality measure between consecutive iterations

@@ -62,6 +62,9 @@ _SIGS = {
     "cubic_rl_plan_set_chunk": ([_vp, _i64], _ci),
     "cubic_rl_plan_chunk": ([_vp], _i64),
     "cubic_rl_deconvolve_noalloc": ([ctypes.POINTER(_i64), _vp, _vp, _ci, _cf, _vp, _vp], _ci),
+    "cubic_rl_noalloc_status": ([_vp], _ci),
+    "cubic_rl_plan_set_wait_limit": ([_vp, ctypes.c_uint64], _ci),
+    "cubic_test_skip_next_tile_copy": ([ctypes.c_uint64], _ci),
     "cubic_rl_deconvolve_batched": ([ctypes.POINTER(_vp), _ci, ctypes.POINTER(_vp), _ci, _cf, ctypes.POINTER(_vp),
                                      _vp], _ci),
     "cubic_rl_batched_graph_nodes": ([], _i64),
@@ -265,6 +268,17 @@ def cubic_rl_stream_status(plan: Plan, stream=None) -> None:
     _check(lib().cubic_rl_stream_status(plan.handle, _stream(stream)), "cubic_rl_stream_status")
 
 
+def cubic_rl_plan_set_wait_limit(plan: Plan, limit_ns: int) -> None:
+    """Limit of every bounded device wait of the plan's kernels, in ns (0: the 2 s default)."""
+    _check(lib().cubic_rl_plan_set_wait_limit(plan.handle, int(limit_ns)), "cubic_rl_plan_set_wait_limit")
+
+
+def cubic_test_skip_next_tile_copy(wait_ns: int) -> None:
+    """Test support: the next TMA-pipelined Y launch in this process has its first CTA skip
+    its first tile copy and wait at most wait_ns for it (see the C header)."""
+    _check(lib().cubic_test_skip_next_tile_copy(int(wait_ns)), "cubic_test_skip_next_tile_copy")
+
+
 def cubic_rl_plan_variants(plan: Plan):
     """((nx, ny, nz) variant counts, (vx, vy, vz) chosen)."""
     c = (_ci * 3)()
@@ -303,6 +317,12 @@ def cubic_rl_deconvolve_noalloc(dims, psf, image, n_iter: int, eps: float, out, 
     _check(lib().cubic_rl_deconvolve_noalloc(d, _ptr(psf, torch.float32, v, "psf"), _ptr(image, torch.float32, v, "image"),
                                              int(n_iter), float(eps), _ptr(out, torch.float32, v, "out"),
                                              _stream(stream)), "cubic_rl_deconvolve_noalloc")
+
+
+def cubic_rl_noalloc_status(stream=None) -> None:
+    """Raises CubicError (CUBIC_ERR_TIMEOUT) if a bounded device wait of an allocation-free
+    call on the current device gave up since the last check; clears the flag."""
+    _check(lib().cubic_rl_noalloc_status(_stream(stream)), "cubic_rl_noalloc_status")
 
 
 def cubic_rl_deconvolve_batched(plans, images, n_iter: int, eps: float, outs, stream=None) -> None:

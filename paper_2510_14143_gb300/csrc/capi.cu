@@ -11,6 +11,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <new>
@@ -132,7 +133,9 @@ __global__ void k_center_to_origin(const float *__restrict__ psf, float *__restr
     }
 }
 
-// Flux sum in double: per-block partial sums, then one block folds them.
+// Flux sum: each thread reads 16-byte vectors and keeps two compensated float32 sums
+// (about twice float precision over its few hundred terms); the threads' sums merge in
+// double per warp and per block, and one block folds the block partials in double.
 constexpr int kReduceThreads = 256;
 constexpr int kReduceBlocks = 1024;
 
@@ -140,9 +143,19 @@ __global__ void __launch_bounds__(kReduceThreads) k_sum_partial(const float *__r
                                                                 double *__restrict__ partial)
 {
     __shared__ double sh[kReduceThreads / 32];
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s += (double)x[i];
+    CFloat a{0.f, 0.f}, b{0.f, 0.f};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // 16-byte vectors where x is 16-byte aligned, then the scalar tail
+    const int64_t n4 = ((uintptr_t)x & 15u) == 0 ? n / 4 : 0;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    for (int64_t i = first; i < n4; i += stride) {
+        const float4 v = __ldg(x4 + i);
+        a = cf_add(cf_add(a, v.x), v.y);
+        b = cf_add(cf_add(b, v.z), v.w);
+    }
+    for (int64_t i = 4 * n4 + first; i < n; i += stride) a = cf_add(a, __ldg(x + i));
+    double s = ((double)a.s - (double)a.c) + ((double)b.s - (double)b.c);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -206,6 +219,7 @@ struct cubic_rl_plan_s {
     int vx = 0, vy = 0, vz = 0; // launch-shape variant of each pass
     int64_t chunk = 0;          // spectrum columns per Y/Z chunk (0: all at once)
     unsigned *err = nullptr;    // device error word (bounded waits), owned
+    unsigned long long wait_ns = 0;  // limit of every bounded device wait (0: 2 s)
     float2 *H = nullptr;        // [nz][ny][xp], owned
     float2 *tw = nullptr;       // twiddles: x | y | z, owned
     float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
@@ -329,10 +343,23 @@ static cudaError_t run_x_as(cubic_rl_plan_s *p, int mode, int kind, const XArgs 
     return counted(p, kind, st, [&] { return p->kx->xv[p->vx].fn[mode](a, st); }, bytes);
 }
 
+// Failure-path test (cubic_test_skip_next_tile_copy): armed with a wait limit, the next
+// Y launch of a TMA-pipelined variant takes it and has its CTA 0 skip its first tile copy.
+static std::atomic<unsigned long long> g_skip_copy_ns{0};
+
 static cudaError_t run_y(cubic_rl_plan_s *p, const YArgs &a, cudaStream_t st)
 {
     const double bytes = 2.0 * 8.0 * (double)p->rows * (double)(a.col1 - a.col0);
-    return counted(p, a.inverse ? KK_Y_INV : KK_Y_FWD, st, [&] { return p->ky->yzv[p->vy].y(a, st); }, bytes);
+    YArgs b = a;
+    const YZVariant &yv = p->ky->yzv[p->vy];
+    if (yv.tma && yv.B > 0 && g_skip_copy_ns.load(std::memory_order_relaxed)) {
+        const unsigned long long ns = g_skip_copy_ns.exchange(0);
+        if (ns) {
+            b.wait_ns = ns;
+            b.skip_first = 1;
+        }
+    }
+    return counted(p, a.inverse ? KK_Y_INV : KK_Y_FWD, st, [&] { return p->ky->yzv[p->vy].y(b, st); }, bytes);
 }
 
 static cudaError_t run_z(cubic_rl_plan_s *p, const ZArgs &a, cudaStream_t st)
@@ -349,6 +376,7 @@ static YArgs y_args(const cubic_rl_plan_s *p, float2 *spec, int inverse, int64_t
 {
     YArgs a{spec, p->tw_y, full ? p->nz : work_planes(p), p->xh, p->xp, inverse, c0, c1, p->err};
     if (!full && p->linear && p->iy < p->ny) (inverse ? a.nstore : a.nload) = p->iy;
+    a.wait_ns = p->wait_ns;
     return a;
 }
 
@@ -366,6 +394,7 @@ static ZArgs z_args(const cubic_rl_plan_s *p, float2 *spec, int mode, float scal
     ZArgs a{spec, p->H, p->tw_z, p->ny, p->xh, p->xp, conv_mode(p, mode), scale, c0, c1, p->err, p->nz,
             p->use_real_h ? p->Hr : nullptr};
     if (!full && p->linear && p->iz < p->nz) a.nload = a.nstore = p->iz;
+    a.wait_ns = p->wait_ns;
     return a;
 }
 
@@ -377,6 +406,7 @@ static XArgs x_args(const cubic_rl_plan_s *p, bool full = false)
     a.rows = full ? p->nz * p->ny : work_planes(p) * work_ny(p);
     a.xp = p->xp;
     a.err = p->err;
+    a.wait_ns = p->wait_ns;
     if (!full && p->linear && p->iy < p->ny) {
         a.ny_img = p->iy;
         a.ny_spec = p->ny;
@@ -1303,6 +1333,19 @@ extern "C" cubic_status_t cubic_rl_stream_status(cubic_rl_plan_t plan, void *str
         CUBIC_CUDA(cudaMemsetAsync(plan->err, 0, sizeof(unsigned), st));
         return fail(CUBIC_ERR_TIMEOUT, "a device wait timed out (error word 0x%x)", word);
     }
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_rl_plan_set_wait_limit(cubic_rl_plan_t plan, uint64_t limit_ns)
+{
+    if (!plan) return fail(CUBIC_ERR_INVALID_ARG, "plan must be non-null");
+    plan->wait_ns = limit_ns;
+    return CUBIC_OK;
+}
+
+extern "C" cubic_status_t cubic_test_skip_next_tile_copy(uint64_t wait_ns)
+{
+    g_skip_copy_ns.store(wait_ns);  // 0 disarms
     return CUBIC_OK;
 }
 
@@ -2835,12 +2878,16 @@ extern "C" int64_t cubic_rl_batched_graph_nodes(void)
 
 // ------------------------------------------------------------------ allocation-free entry point
 //
-// For callers that must not allocate device memory: code running while another
-// framework captures a stream into a CUDA graph, processes whose device memory is
-// entirely reserved by a pool allocator, and latency-critical callers that cannot
-// afford cudaMalloc's implicit device synchronisation.  Everything a deconvolution
-// needs beyond its inputs and outputs (PSF spectrum, work spectrum, twiddles,
-// reduction partials, error word) lives in one fixed file-scope device array.
+// For callers that cannot call cudaMalloc: frameworks whose device memory is entirely
+// reserved by their own pool allocator, plug-in code that its host application does not
+// let allocate, and latency-critical loops that cannot take cudaMalloc's implicit
+// device-wide synchronisation.  Everything a deconvolution needs beyond its inputs and
+// outputs (PSF spectrum, work spectrum, twiddles, reduction partials, error word) lives
+// in one fixed file-scope device array.
+//
+// Layout of the array: the device error word alone in the first 256 bytes, at the same
+// place for every volume shape (so a timeout stays there until it is read), then H, the
+// work spectrum, the twiddles and the reduction partials of the current call.
 
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB per device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -2849,6 +2896,25 @@ static std::mutex g_noalloc_mu;
 static unsigned char *g_noalloc_ptr[64];  // device address of the array, per device ordinal
 
 static size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+// The array's device address on the current device, looked up once per device (with that
+// device current) and kept for the life of the process.
+static cubic_status_t noalloc_base(unsigned char **base, int *device)
+{
+    int dev = 0;
+    CUBIC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CUBIC_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *addr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+        if (e != cudaSuccess || !addr) return fail(CUBIC_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = (unsigned char *)addr;
+    }
+    *base = g_noalloc_ptr[dev];
+    *device = dev;
+    return CUBIC_OK;
+}
 
 extern "C" cubic_status_t cubic_rl_deconvolve_noalloc(const int64_t dims[3], const float *psf, const float *image,
                                                       int n_iter, float eps, float *out, void *stream)
@@ -2863,7 +2929,9 @@ extern "C" cubic_status_t cubic_rl_deconvolve_noalloc(const int64_t dims[3], con
     if (!aligned16(psf) || !aligned16(image) || !aligned16(out))
         return fail(CUBIC_ERR_ALIGNMENT, "psf, image and out must be 16-byte aligned");
 
-    // a plan that lives on this stack frame; its device buffers are carved out of the array
+    // a plan that lives on this stack frame; its device buffers are carved out of the array.
+    // It never takes the real-spectrum Z passes: deciding that the PSF is point-symmetric
+    // takes a host synchronisation, so H stays complex (same result to float rounding)
     cubic_rl_plan_s p;
     p.nz = dims[0];
     p.ny = dims[1];
@@ -2877,53 +2945,58 @@ extern "C" cubic_status_t cubic_rl_deconvolve_noalloc(const int64_t dims[3], con
     p.kz = find_axis(p.nz);
     if (overlaps(image, out, (size_t)p.V * sizeof(float)))
         return fail(CUBIC_ERR_INVALID_ARG, "out must not overlap image");
+    const size_t err_bytes = 256;
     const size_t spec_bytes = align256(spec_elems(&p) * sizeof(float2));
     const size_t tw_bytes = align256((size_t)(p.nx + p.ny + p.nz) * sizeof(float2));
     const size_t red_bytes = align256((kReduceBlocks + 1) * sizeof(double));
-    const size_t need = 2 * spec_bytes + tw_bytes + red_bytes + 256;
+    const size_t need = err_bytes + 2 * spec_bytes + tw_bytes + red_bytes;
     if (need > kNoAllocScratchBytes)
         return fail(CUBIC_ERR_UNSUPPORTED_SIZE,
                     "volume needs %zu bytes of scratch; the allocation-free entry point has %zu "
                     "(nz*ny*(nx/2+1 rounded up to 16) must stay below about 2^19)",
                     need, kNoAllocScratchBytes);
 
-    // once per device, with that device current: the array's device address
-    int dev = 0;
-    CUBIC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(CUBIC_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
-    unsigned char *base;
-    {
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void *addr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-            if (e != cudaSuccess || !addr)
-                return fail(CUBIC_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            g_noalloc_ptr[dev] = (unsigned char *)addr;
-        }
-        base = g_noalloc_ptr[dev];
-    }
-    p.device = dev;
-    p.H = (float2 *)base;
-    p.ws = (float2 *)(base + spec_bytes);
+    unsigned char *base = nullptr;
+    cubic_status_t s = noalloc_base(&base, &p.device);
+    if (s != CUBIC_OK) return s;
+    p.err = (unsigned *)base;
+    p.H = (float2 *)(base + err_bytes);
+    p.ws = (float2 *)(base + err_bytes + spec_bytes);
     p.own_ws = false;
-    p.tw = (float2 *)(base + 2 * spec_bytes);
+    p.tw = (float2 *)(base + err_bytes + 2 * spec_bytes);
     p.tw_x = p.tw;
     p.tw_y = p.tw + p.nx;
     p.tw_z = p.tw + p.nx + p.ny;
-    p.partial = (double *)(base + 2 * spec_bytes + tw_bytes);
-    p.err = (unsigned *)(base + 2 * spec_bytes + tw_bytes + red_bytes);
+    p.partial = (double *)(base + err_bytes + 2 * spec_bytes + tw_bytes);
     tuned_variants(&p);
 
+    // The array keeps the previous call's contents.  Everything but the error word is
+    // rewritten below before it is read; the error word starts at zero (static
+    // initialisation) and only cubic_rl_noalloc_status clears it.
     cudaStream_t st = (cudaStream_t)stream;
-    // the array keeps the previous call's contents: the error word must start at zero,
-    // everything else is rewritten below before it is read
-    CUBIC_CUDA(cudaMemsetAsync(p.err, 0, sizeof(unsigned), st));
     k_twiddles<<<grid_for(p.nx, 128, 1 << 20), 128, 0, st>>>(p.tw_x, (int)p.nx);
     k_twiddles<<<grid_for(p.ny, 128, 1 << 20), 128, 0, st>>>(p.tw_y, (int)p.ny);
     k_twiddles<<<grid_for(p.nz, 128, 1 << 20), 128, 0, st>>>(p.tw_z, (int)p.nz);
     CUBIC_CUDA(cudaGetLastError());
-    cubic_status_t s = load_psf(&p, psf, st);
+    s = load_psf(&p, psf, st);
     if (s != CUBIC_OK) return s;
     return enqueue_rl(&p, image, n_iter, eps, out, p.ws, st);
+}
+
+extern "C" cubic_status_t cubic_rl_noalloc_status(void *stream)
+{
+    unsigned char *base = nullptr;
+    int dev = 0;
+    cubic_status_t s = noalloc_base(&base, &dev);
+    if (s != CUBIC_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned word = 0;
+    CUBIC_CUDA(cudaMemcpyAsync(&word, base, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CUBIC_CUDA(cudaStreamSynchronize(st));
+    if (word) {
+        CUBIC_CUDA(cudaMemsetAsync(base, 0, sizeof(unsigned), st));
+        CUBIC_CUDA(cudaStreamSynchronize(st));
+        return fail(CUBIC_ERR_TIMEOUT, "a device wait of an allocation-free call timed out (error word 0x%x)", word);
+    }
+    return CUBIC_OK;
 }

@@ -31,6 +31,10 @@ struct ColArgs {
     float scale;         // ZM_FWD_SCALE / ZM_INV_SCALE
     unsigned *err;
     int nstore;          // line rows stored (boxes starting at or past it are skipped); N: all
+    unsigned long long wait_ns;  // limit of the tile waits (0: kWaitNs)
+    // failure-path test: CTA 0 does not issue the copy of its first tile, so its first
+    // wait runs out (nothing is left in flight: that copy never starts)
+    int skip_first;
 };
 
 // largest divisor of n that is <= 256 (TMA box extent limit)
@@ -189,7 +193,8 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
     const int64_t first = blockIdx.x, step = gridDim.x;
     if (threadIdx.x == 0)
         for (int i = 0; i < D; ++i)
-            if (first + i * step < a.ntiles) issue(first + i * step, i % NS);
+            if (first + i * step < a.ntiles && !(i == 0 && a.skip_first && blockIdx.x == 0))
+                issue(first + i * step, i % NS);
 
     int it = 0;
     for (int64_t tile = first; tile < a.ntiles; tile += step, ++it) {
@@ -200,9 +205,10 @@ __global__ void __launch_bounds__(P *B) k_colpass_tma(const __grid_constant__ CU
             bulk_wait_read<KW>();  // the stage being refilled has left shared memory
             issue(ahead, (it + D) % NS);
         }
-        const bool arrived = mbar_wait_bounded(&full[s], phase, a.err);
+        const bool arrived = mbar_wait_bounded(&full[s], phase, a.err, a.wait_ns);
         if (!__syncthreads_and(arrived)) {
-            // give already issued loads a bounded chance to land before leaving
+            // give already issued loads a bounded chance (the default limit, not the
+            // launch's) to land before leaving
             if (threadIdx.x == 0)
                 for (int i = 1; i <= D; ++i)
                     if (tile + (int64_t)i * step < a.ntiles)

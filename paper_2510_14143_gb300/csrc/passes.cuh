@@ -47,6 +47,7 @@ struct XArgs {
     int64_t xp;        // spectrum pitch (complex elements)
     float eps;
     unsigned *err;     // device error word (bounded waits)
+    unsigned long long wait_ns;  // limit of the bounded waits (0: kWaitNs)
     // optional copies of intermediates (null: not stored), used by the gradient's
     // recomputation: XM_RATIO stores b (keep_a) and r (keep_b); XM_UPDATE / XM_FINAL
     // store q (keep_a)
@@ -90,6 +91,8 @@ struct YArgs {
     // linear-boundary plans: rows of each line that are loaded (the rest reads as zero)
     // and stored; 0: all N
     int64_t nload, nstore;
+    unsigned long long wait_ns;  // TMA variants: limit of the tile waits (0: kWaitNs)
+    int skip_first;              // TMA variants: the failure-path test of ColArgs
 };
 
 // ZM_MUL_REAL: product with a real H (point-symmetric PSF), where convolution and
@@ -121,6 +124,8 @@ struct ZArgs {
     float2 *gacc;
     const float2 *gother;
     int gconj;
+    unsigned long long wait_ns;  // TMA variants: limit of the tile waits (0: kWaitNs)
+    int skip_first;              // TMA variants: the failure-path test of ColArgs
 };
 
 // ------------------------------------------------------------------ X pass
@@ -348,7 +353,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             });
         }
     } else {
-        const bool landed = mbar_wait_bounded(&bar[1], 0, a.err);
+        const bool landed = mbar_wait_bounded(&bar[1], 0, a.err, a.wait_ns);
         if (!__syncthreads_and(landed)) return;
         const float2 *q0 = lpair, *q1 = lpair + XB;
         static_for<0, E>([&](auto i_) {
@@ -374,7 +379,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
         // operand rows: shared memory (TMA) or global
         const float *p0, *p1;
         if constexpr (kTma) {
-            const bool arrived = mbar_wait_bounded(&bar[0], 0, a.err);
+            const bool arrived = mbar_wait_bounded(&bar[0], 0, a.err, a.wait_ns);
             if (!__syncthreads_and(arrived)) return;
             p0 = oprows + (2 * l) * N;
             p1 = oprows + (2 * l + 1) * N;

@@ -183,7 +183,8 @@ int col_grid_cap()
 template <int N, int P, int B, int KIND, int NS, bool HREAL = false>
 cudaError_t launch_col(const float2 *spec, const float2 *H, const float *Hr, int64_t nz, int64_t ny, int64_t xp,
                        int64_t col0, int64_t col1, int64_t outer, const float2 *tw, int mode, float scale,
-                       unsigned *err, cudaStream_t st, int64_t nload = 0, int64_t nstore = 0)
+                       unsigned *err, cudaStream_t st, int64_t nload = 0, int64_t nstore = 0,
+                       unsigned long long wait_ns = 0, int skip_first = 0)
 {
     constexpr int R = box_rows(N);
     constexpr size_t smem = col_smem_bytes<N, P, B, KIND, NS, HREAL>();
@@ -228,6 +229,8 @@ cudaError_t launch_col(const float2 *spec, const float2 *H, const float *Hr, int
     c.scale = scale;
     c.err = err;
     c.nstore = (int)ns;
+    c.wait_ns = wait_ns;
+    c.skip_first = skip_first;
     if (c.ntiles == 0) return cudaSuccess;
     const int64_t cap = col_grid_cap<N, P, B, KIND, NS, HREAL>();
     const unsigned grid = (unsigned)(c.ntiles < cap ? c.ntiles : cap);
@@ -238,7 +241,7 @@ template <int N, int P, int B, int NS>
 cudaError_t launch_y_tma(const YArgs &a, cudaStream_t st)
 {
     return launch_col<N, P, B, COL_Y, NS>(a.spec, nullptr, nullptr, a.nz, N, a.xp, a.col0, a.col1, a.nz, a.tw, a.inverse, 1.f,
-                                      a.err, st, a.nload, a.nstore);
+                                      a.err, st, a.nload, a.nstore, a.wait_ns, a.skip_first);
 }
 
 template <int N, int P, int B, int NS>
@@ -247,9 +250,10 @@ cudaError_t launch_z_tma(const ZArgs &a, cudaStream_t st)
     const bool needH = a.mode == ZM_CONV || a.mode == ZM_CORR;
     if (a.mode == ZM_MUL_REAL)
         return launch_col<N, P, B, COL_Z, NS, true>(a.spec, nullptr, a.Hr, N, a.ny, a.xp, a.col0, a.col1, a.ny,
-                                                    a.tw, a.mode, a.scale, a.err, st, a.nload, a.nstore);
+                                                    a.tw, a.mode, a.scale, a.err, st, a.nload, a.nstore, a.wait_ns,
+                                                    a.skip_first);
     return launch_col<N, P, B, COL_Z, NS>(a.spec, needH ? a.H : nullptr, a.Hr, N, a.ny, a.xp, a.col0, a.col1, a.ny, a.tw,
-                                      a.mode, a.scale, a.err, st, a.nload, a.nstore);
+                                      a.mode, a.scale, a.err, st, a.nload, a.nstore, a.wait_ns, a.skip_first);
 }
 
 // Y and Z tile widths and stage counts may differ: the Z pass also stages H.

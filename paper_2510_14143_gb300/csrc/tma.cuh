@@ -1,9 +1,10 @@
 // tma.cuh -- bulk asynchronous copies (TMA, cp.async.bulk) from global to
 // shared memory, completed on an mbarrier, with bounded waits.
 //
-// Every wait here gives up after kWaitNs nanoseconds of %globaltimer: it then
-// sets a bit in the caller's device error word and reports failure, so a
-// kernel never spins forever.  The host maps a set word to CUBIC_ERR_TIMEOUT.
+// Every wait here gives up after a limit of %globaltimer nanoseconds (kWaitNs,
+// 2 s, unless the launch carries its own): it then sets a bit in the caller's
+// device error word and reports failure, so a kernel never spins forever.  The
+// host maps a set word to CUBIC_ERR_TIMEOUT.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -78,14 +79,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
     return done != 0;
 }
 
-// Wait for phase `phase` of `bar` to complete, at most kWaitNs.  On timeout
-// sets kDevErrTimeout in *err and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase, unsigned *err)
+// Wait for phase `phase` of `bar` to complete, at most limit_ns (0: kWaitNs).  On
+// timeout sets kDevErrTimeout in *err and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase, unsigned *err,
+                                                  unsigned long long limit_ns = 0)
 {
     if (mbar_try_wait(bar, phase)) return true;
+    const unsigned long long lim = limit_ns ? limit_ns : kWaitNs;
     const unsigned long long t0 = global_timer_ns();
     while (!mbar_try_wait(bar, phase)) {
-        if (global_timer_ns() - t0 > kWaitNs) {
+        if (global_timer_ns() - t0 > lim) {
             if (err) atomicOr(err, kDevErrTimeout);
             return false;
         }

@@ -70,3 +70,5 @@ def test_invalid_arguments_fail_before_any_launch(libpath):
     assert lib.cubic_rl_plan(ctypes.byref(h), dims, ctypes.c_void_p(258), 0, None) == 3
     assert lib.cubic_rl_plan(ctypes.byref(h), dims, ctypes.c_void_p(256), 1, None) == 1
     assert lib.cubic_rl_deconvolve(None, ctypes.c_void_p(256), 1, 1e-6, ctypes.c_void_p(512), None) == 1
+    lib.cubic_rl_plan_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    assert lib.cubic_rl_plan_set_wait_limit(None, 1) == 1

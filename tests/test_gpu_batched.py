@@ -83,10 +83,14 @@ def test_batched_matches_oracle_and_replays(cr):
 
 
 def test_batched_workload_sample(cr):
-    # the 64-volume workload's first volumes (its sizes and generator), 50 iterations, vs the oracle
-    shapes = synth.batch_shapes()[:3]
+    # eight volumes of the 64-volume workload (every eighth, from the first: its sizes and
+    # generator), one batched call of its 50 iterations, each volume vs the oracle in relative
+    # L2 and in the worst voxel (the benchmark's accuracy leg checks the eight from the fifth)
+    all_shapes = synth.batch_shapes()
+    picks = list(range(0, len(all_shapes), 8))
+    shapes = [all_shapes[j] for j in picks]
     plans, imgs, vols = [], [], []
-    for j, shape in enumerate(shapes):
+    for j, shape in zip(picks, shapes):
         d, _ = synth.batch_volume(j, shape)
         psf = torch.empty(shape, dtype=torch.float32, device="cuda")
         cr.cubic_psf_gaussian(shape, synth.SMALL.psf_sigma_xy, synth.SMALL.psf_sigma_z, 1.0, psf)
@@ -98,7 +102,9 @@ def test_batched_workload_sample(cr):
     torch.cuda.synchronize()
     for (d, psf), out in zip(vols, outs):
         ref = oracle.rl(d, psf, synth.BATCH_ITERS, 1e-6)
-        assert rel_l2(out.cpu().numpy(), ref) <= 1e-4
+        got = out.cpu().numpy().astype(np.float64)
+        assert rel_l2(got, ref) <= 1e-4
+        assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
 
 
 def test_batched_errors(cr):

@@ -1,8 +1,10 @@
 """The 1024x1024x128 workload in the launch configuration the benchmark times (autotuned
 shapes, Gaussian PSF with a real spectrum).
 
-Two iterations are compared with the FP64 oracle over the whole volume.  The benchmarked
-50 iterations are checked through properties that hold at any size: flux conservation
+Two iterations are compared with the FP64 oracle over the whole volume (relative L2 and
+the worst voxel).  The benchmarked 50 iterations are compared with the oracle by the
+benchmark's accuracy leg (minutes of CPU); here they are checked through properties that
+hold at any size: flux conservation
 (every RL step keeps sum(u) = sum(d) for a normalised PSF while the clamp is inactive)
 and nonnegativity.  The host-buffer entry point must give the device path's result bitwise.
 """
@@ -47,9 +49,13 @@ def test_large_two_iterations_match_oracle(cr, large):
     cr.cubic_rl_deconvolve(plan, dd, 2, 1e-6, out)
     torch.cuda.synchronize()
     ref = oracle.rl(d, psf.cpu().numpy(), 2, 1e-6)
-    err = rel_l2(out.cpu().numpy(), ref)
-    print(f"rl 1024x1024x128, 2 it, tuned shapes {cr.cubic_rl_plan_variants(plan)[1]}: rel-L2 = {err:.3e}")
+    got = out.cpu().numpy().astype(np.float64)
+    err = rel_l2(got, ref)
+    worst = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    print(f"rl 1024x1024x128, 2 it, tuned shapes {cr.cubic_rl_plan_variants(plan)[1]}: rel-L2 = {err:.3e}, "
+          f"max rel = {worst:.3e}")
     assert err <= 1e-5
+    assert worst <= 1e-5
 
 
 def test_large_benchmarked_run_properties(cr, large):

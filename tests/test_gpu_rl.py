@@ -163,16 +163,24 @@ def test_rl_delta_psf_identity(cr):
     assert rel_l2(got, d) < 1e-6
 
 
+def max_rel(a, b):
+    # the worst voxel against the volume's scale: max |a - b| / max |b|
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / np.max(np.abs(b)))
+
+
 def test_rl_medium_workload_parity(cr):
-    # 256x256x128 at 10 iterations against the oracle (the full 100 are timed by the bench)
+    # 256x256x128 at its stated 100 iterations against the oracle, in relative L2 and in
+    # the worst voxel (the float32 error grows with the iteration count; 1e-4 is the stated
+    # precision target)
     w = synth.MEDIUM
     d, _ = synth.workload_volume(w)
     psf = oracle.psf_gaussian(d.shape, w.psf_sigma_xy, w.psf_sigma_z).astype(np.float32)
-    got = run_rl(cr, d, psf, 10)
-    ref = oracle.rl(d, psf, 10, 1e-6)
-    err = rel_l2(got, ref)
-    print(f"rl 256x256x128, 10 it: rel-L2 = {err:.3e}")
+    got = run_rl(cr, d, psf, w.n_iter)
+    ref = oracle.rl(d, psf, w.n_iter, 1e-6)
+    err, worst = rel_l2(got, ref), max_rel(got, ref)
+    print(f"rl 256x256x128, {w.n_iter} it: rel-L2 = {err:.3e}, max rel = {worst:.3e}")
     assert err <= 1e-4
+    assert worst <= 1e-4
 
 
 def test_rl_paper_shape_parity(cr):
@@ -184,9 +192,10 @@ def test_rl_paper_shape_parity(cr):
     psf = oracle.psf_gaussian(w.shape, w.psf_sigma_xy, w.psf_sigma_z).astype(np.float32)
     got = run_rl(cr, d, psf, 2)
     ref = oracle.rl(d, psf, 2, 1e-6)
-    err = rel_l2(got, ref)
-    print(f"rl 2560x2160x30, 2 it: rel-L2 = {err:.3e}")
+    err, worst = rel_l2(got, ref), max_rel(got, ref)
+    print(f"rl 2560x2160x30, 2 it: rel-L2 = {err:.3e}, max rel = {worst:.3e}")
     assert err <= 1e-5
+    assert worst <= 1e-5
 
 
 def test_errors_are_reported(cr):
