@@ -549,17 +549,24 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     }
 
     if constexpr (MODE == XM_FWD || MODE == XM_RATIO || MODE == XM_UPDATE) {
-        FFT::forward(v, sm, stw, t, sync);
+        // On lines longer than 1024 with more than 16 elements per thread, the passes that
+        // run two transforms would keep every exchange address of the inverse transform
+        // live across the pointwise step for reuse in the forward one (about 165 registers
+        // at length 2560).  An opaque copy of the thread index makes the compiler recompute
+        // them instead (96 registers).  Shorter lines do better without it.
+        int tf = t;
+        if constexpr (N > 1024 && E > 16 && MODE != XM_FWD) asm volatile("" : "+r"(tf));
+        FFT::forward(v, sm, stw, tf, sync);
         // split the packed spectrum into the two rows' half spectra
         static_for<0, E>([&](auto i_) {
             constexpr int i = CUBIC_CI(i_);
-            sm.at(t + P * i) = v[i];
+            sm.at(tf + P * i) = v[i];
         });
         sync();
         float2 *q0 = a.spec_out + srow(r0) * a.xp, *q1 = a.spec_out + srow(r1) * a.xp;
         static_for<0, E>([&](auto i_) {
             constexpr int i = CUBIC_CI(i_);
-            const int k = t + P * i;
+            const int k = tf + P * i;
             if (2 * k <= N) {
                 const float2 zk = v[i];
                 const float2 zn = sm.at(k == 0 ? 0 : N - k);
@@ -619,11 +626,11 @@ __global__ void __launch_bounds__(P * L) k_xpass(XArgs a, const MultiTable<XArgs
 
 // The prefetching ratio and update kernels exist to fit more CTAs on an SM: they are
 // held to the register count of 28 resident warps (72 registers) for up to 16 elements
-// per thread, else of 16 warps (128 registers).
+// per thread, of 16 warps (128 registers) up to 32, else of 12 warps (168 registers).
 template <int N, int P, int L>
 constexpr int x_pf_min_blocks()
 {
-    constexpr int threads = N / P <= 16 ? 896 : 512;
+    constexpr int threads = N / P <= 16 ? 896 : N / P <= 32 ? 512 : 384;
     return P * L <= threads / 2 ? threads / (P * L) : 1;
 }
 

@@ -63,6 +63,10 @@ const AxisKernels *find_axis(int64_t n);
 
 // ------------------------------------------------------------------ launchers
 
+// Set while this thread captures a graph whose launches carry their own dependencies
+// (the batched path): launches then go without the programmatic attribute.
+inline thread_local bool t_plain_launch = false;
+
 // Launch with programmatic stream serialization: the kernel may start while its
 // predecessor in the stream is still running (its CTAs wait in pdl_wait before
 // touching the predecessor's output), which hides launch latency and prologues.
@@ -79,7 +83,7 @@ inline cudaError_t launch_pdl(void (*fn)(KArgs...), dim3 grid, dim3 block, size_
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = t_plain_launch ? 0 : 1;
     return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
 }
 
@@ -426,7 +430,17 @@ AxisKernels make_axis()
     // lines longer than 1024: a split with up to 40 elements per thread may need fewer
     // stages (2560: 40 x 8 x 8 instead of 20 x 4 x 4 x 4 x 2)
     constexpr int PW = N > 1024 ? choose_threads(N, 40) : -1;
-    if constexpr (PW > 0 && PW != P0 && PW != S::P1) push_x(k, make_xvariant<N, PW, S::lines(PW, 128)>());
+    if constexpr (PW > 0 && PW != P0 && PW != S::P1) {
+        push_x(k, make_xvariant<N, PW, S::lines(PW, 128)>());
+        // its operand rows through L2: no staged rows, one CTA more per SM
+        if constexpr (N % 4 == 0) push_x(k, make_xvariant<N, PW, S::lines(PW, 128), true, true>());
+    }
+    // lines longer than 1024 hold one line pair per CTA in the default split (72 to 128
+    // threads): two line pairs share one copy of the stage twiddle table
+    if constexpr (N > 1024 && S::lines(P0, 128) == 1 && 2 * P0 <= 512) {
+        push_x(k, make_xvariant<N, P0, 2>());
+        if constexpr (N % 4 == 0) push_x(k, make_xvariant<N, P0, 2, true, true>());
+    }
     // long lines: the default split with the ratio and/or the update reading their
     // operand rows through L2 (less shared memory per CTA, more CTAs per SM)
     if constexpr (N >= 256 && N % 4 == 0) {
@@ -435,6 +449,9 @@ AxisKernels make_axis()
         push_x(k, make_xvariant<N, PX, LX, true, true>());
         push_x(k, make_xvariant<N, PX, LX, true, false>());
         push_x(k, make_xvariant<N, PX, LX, false, true>());
+        // the split with more elements per thread (fewer stages, fewer instructions) is held
+        // to few CTAs per SM by its staged operand rows: both prefetched
+        if constexpr (S::kAlt && N <= 1024) push_x(k, make_xvariant<N, P0, S::lines(P0, 128), true, true>());
     }
     constexpr int XL = S::lines(P0, 128);
     k.xm[XM_FWD] = launch_x_multi<N, P0, XL, XM_FWD>;
