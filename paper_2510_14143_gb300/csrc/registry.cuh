@@ -63,10 +63,6 @@ const AxisKernels *find_axis(int64_t n);
 
 // ------------------------------------------------------------------ launchers
 
-// Set while this thread captures a graph whose launches carry their own dependencies
-// (the batched path): launches then go without the programmatic attribute.
-inline thread_local bool t_plain_launch = false;
-
 // Launch with programmatic stream serialization: the kernel may start while its
 // predecessor in the stream is still running (its CTAs wait in pdl_wait before
 // touching the predecessor's output), which hides launch latency and prologues.
@@ -83,7 +79,7 @@ inline cudaError_t launch_pdl(void (*fn)(KArgs...), dim3 grid, dim3 block, size_
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = t_plain_launch ? 0 : 1;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
 }
 
