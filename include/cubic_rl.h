@@ -334,7 +334,8 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve_ckpt(cubic_rl_plan_t plan, const fl
                                                   void *stream);
 
 /* Device scratch the backward keeps in the plan for this checkpoint spacing:
- * (4*ckpt_every + 5) volumes of floats plus three half spectra. */
+ * (4*ckpt_every + 4) volumes of floats, (2*ckpt_every + 1) half spectra and a small
+ * reduction buffer. */
 CUBIC_API cubic_status_t cubic_rl_backward_workspace_bytes(cubic_rl_plan_t plan, int ckpt_every,
                                                            size_t *bytes);
 

@@ -203,12 +203,13 @@ static unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 32)
 enum KernelKind : int {
     KK_SUM = 0, KK_FILL, KK_SHIFT, KK_X_FWD, KK_X_INV, KK_X_RATIO, KK_X_UPDATE, KK_X_FINAL,
     KK_Y_FWD, KK_Y_INV, KK_Z_FWD, KK_Z_INV, KK_Z_CONV, KK_Z_CORR,
-    KK_X_ACC_UPDATE, KK_X_ACC_PREDICT, KK_ACC_ALPHA, KK_COUNT
+    KK_X_ACC_UPDATE, KK_X_ACC_PREDICT, KK_ACC_ALPHA, KK_X_ADJOINT, KK_COUNT
 };
 
 static const char *const kKindNames[KK_COUNT] = {
     "sum", "fill_initial", "center_to_origin", "x_fwd", "x_inv", "x_ratio", "x_update", "x_final",
-    "y_fwd", "y_inv", "z_fwd", "z_inv", "z_conv", "z_corr", "x_acc_update", "x_acc_predict", "acc_alpha"};
+    "y_fwd", "y_inv", "z_fwd", "z_inv", "z_conv", "z_corr", "x_acc_update", "x_acc_predict", "acc_alpha",
+    "x_adjoint"};
 
 // ------------------------------------------------------------------ plan
 
@@ -304,6 +305,7 @@ static double kind_bytes(const cubic_rl_plan_s *p, int kind)
     case KK_X_ACC_UPDATE: return spec + 4 * real;
     case KK_X_ACC_PREDICT: return 3 * real + spec;
     case KK_ACC_ALPHA: return 0.0;
+    case KK_X_ADJOINT: return spec + 3 * real;  // each adjoint pass gives its own count
     }
     return 0.0;
 }
@@ -1362,35 +1364,6 @@ extern "C" cubic_status_t cubic_test_skip_next_tile_copy(uint64_t wait_ns)
 // recomputes each segment from its checkpoint, keeping u, b, r and q of every
 // iteration of the segment, then walks the segment backwards.
 
-__global__ void k_adj_q(const float *__restrict__ g, const float *__restrict__ u, const float *__restrict__ q,
-                        float *__restrict__ qbar, float *__restrict__ ubar, int64_t V)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        qbar[i] = gi * u[i];
-        ubar[i] = gi * q[i];
-    }
-}
-
-// in: rbar (in bbar's buffer); out: bbar; dbar += rbar / c
-__global__ void k_adj_r(const float *__restrict__ b, const float *__restrict__ d, float *__restrict__ rb,
-                        float *__restrict__ dbar, float eps, int64_t V)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
-        const float bi = b[i];
-        const float c = fmaxf(bi, eps);
-        const float r = rb[i];
-        dbar[i] += r / c;
-        rb[i] = bi > eps ? -r * d[i] / (c * c) : 0.f;
-    }
-}
-
-__global__ void k_add(float *__restrict__ a, const float *__restrict__ b, int64_t V)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x)
-        a[i] += b[i];
-}
-
 // Compensated float32 sum of x over V elements: block partials (CFloat) ...
 __global__ void __launch_bounds__(kReduceThreads) k_csum_partial(const float *__restrict__ x, int64_t V,
                                                                  CFloat *__restrict__ partial)
@@ -1568,8 +1541,8 @@ extern "C" cubic_status_t cubic_rl_backward_workspace_bytes(cubic_rl_plan_t plan
     const size_t vb = ((size_t)plan->V * sizeof(float) + 255) / 256 * 256;
     const size_t sb = (spec_elems(plan) * sizeof(float2) + 255) / 256 * 256;
     const size_t rb = ((kReduceBlocks + 1) * sizeof(double) + 255) / 256 * 256;
-    // u (c + 1), b, r, q (c each), g, ubar, tmp, dbar; spectra U, R (c each) and G
-    *bytes = vb * (4 * (size_t)ckpt_every + 1 + 4) + (2 * (size_t)ckpt_every + 1) * sb + rb;
+    // u (c + 1), b, r, q (c each), g, tmp, dbar; spectra U, R (c each) and G
+    *bytes = vb * (4 * (size_t)ckpt_every + 1 + 3) + (2 * (size_t)ckpt_every + 1) * sb + rb;
     return CUBIC_OK;
 }
 
@@ -1609,15 +1582,14 @@ extern "C" cubic_status_t cubic_rl_backward(cubic_rl_plan_t plan, const float *i
     for (int j = 0; j <= c; ++j) seg_u[j] = (float *)(m + vb * j);
     for (int j = 0; j < c; ++j) {
         seg_b[j] = (float *)(m + vb * (c + 1 + j));
-        seg_r[j] = (float *)(m + vb * (2 * c + 1 + j));
+        seg_r[j] = (float *)(m + vb * (2 * c + 1 + j));  // written by the ratio pass with b
         seg_q[j] = (float *)(m + vb * (3 * c + 1 + j));
     }
-    float *g = (float *)(m + vb * (4 * c + 1));     // dL/du of the current iteration
-    float *ubar = (float *)(m + vb * (4 * c + 2));
-    float *tmp = (float *)(m + vb * (4 * c + 3));   // qbar, then rbar / bbar
-    float *dbar = (float *)(m + vb * (4 * c + 4));
+    float *g = (float *)(m + vb * (4 * c + 1));     // the running gradient of the iterate
+    float *tmp = (float *)(m + vb * (4 * c + 2));   // the PSF gradient, back in real space
+    float *dbar = (float *)(m + vb * (4 * c + 3));
     std::vector<float2 *> seg_U(c), seg_R(c);
-    unsigned char *specs = m + vb * (4 * c + 5);
+    unsigned char *specs = m + vb * (4 * c + 4);
     for (int j = 0; j < c; ++j) {
         seg_U[j] = (float2 *)(specs + sb * j);
         seg_R[j] = (float2 *)(specs + sb * (c + j));
@@ -1639,26 +1611,45 @@ extern "C" cubic_status_t cubic_rl_backward(cubic_rl_plan_t plan, const float *i
         if ((s = enqueue_segment(p, image, eps, cnt, seg_u.data(), seg_b.data(), seg_r.data(), seg_q.data(), spec,
                                  st, seg_U.data(), seg_R.data())) != CUBIC_OK)
             return s;
+        // The adjoint iterations as fused pass chains: every pointwise step rides in an X
+        // pass (XM_ADJ_*), so an iteration is 8 passes, like a forward one.  One buffer, g,
+        // carries the running gradient of the iterate through the segment.
         XArgs xa = x_args(p);
-        xa.spec_in = spec;
         xa.spec_out = spec;
-        xa.src = tmp;
-        xa.dst = tmp;
+        xa.d = image;
+        xa.eps = eps;
+        const double real = (double)V * 4.0, cplx = (double)p->rows * p->xh * 8.0;
+        auto adj = [&](int mode, const XArgs &a, double bytes) {
+            return counted(p, KK_X_ADJOINT, st, [&] { return p->kx->adj[mode - XM_ADJ_R](a, st); }, bytes);
+        };
+        XArgs au = xa;
+        au.adj_w = g;
+        {
+            // the segment's last iteration: qbar = g u (its spectrum), g = g q
+            XArgs a0 = au;
+            a0.adj_u = seg_u[cnt - 1];
+            a0.adj_q = seg_q[cnt - 1];
+            CUBIC_CUDA(adj(XM_ADJ_U, a0, 4 * real + cplx));
+        }
         for (int j = cnt - 1; j >= 0; --j) {
-            // qbar = g u, ubar = g q
-            k_adj_q<<<gr, 256, 0, st>>>(g, seg_u[j], seg_q[j], tmp, ubar, V);
             // rbar = h * qbar, with G += conj(Qbar) R in its z pass
-            CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
             if ((s = enqueue_yzy_grad(p, spec, ZM_CONV, nullptr, G, seg_R[j], 1, st)) != CUBIC_OK) return s;
-            CUBIC_CUDA(run_x(p, XM_INV, xa, st));
-            // dbar += rbar / c; bbar
-            k_adj_r<<<gr, 256, 0, st>>>(seg_b[j], image, tmp, dbar, eps, V);
-            // ubar += h (x) bbar, with G += Bbar conj(U) in its z pass
-            CUBIC_CUDA(run_x(p, XM_FWD, xa, st));
+            // dbar += rbar / c; the spectrum of bbar
+            XArgs ar = xa;
+            ar.spec_in = spec;
+            ar.adj_b = seg_b[j];
+            ar.adj_dbar = dbar;
+            CUBIC_CUDA(adj(XM_ADJ_R, ar, 4 * real + 2 * cplx));
+            // h (x) bbar, with G += Bbar conj(U) in its z pass
             if ((s = enqueue_yzy_grad(p, spec, ZM_CORR, nullptr, G, seg_U[j], 0, st)) != CUBIC_OK) return s;
-            CUBIC_CUDA(run_x(p, XM_INV, xa, st));
-            k_add<<<gr, 256, 0, st>>>(ubar, tmp, V);
-            std::swap(g, ubar);  // g = dL/du_k
+            // g += h (x) bbar: dL/du_j; then the previous iteration's qbar and g q
+            XArgs a1 = au;
+            a1.spec_in = spec;
+            if (j > 0) {
+                a1.adj_u = seg_u[j - 1];
+                a1.adj_q = seg_q[j - 1];
+            }
+            CUBIC_CUDA(adj(XM_ADJ_U, a1, (j > 0 ? 4 * real : 2 * real) + (j > 0 ? 2 : 1) * cplx));
         }
         CUBIC_CUDA(cudaGetLastError());
     }

@@ -32,7 +32,10 @@ enum XMode : int {
     XM_RATIO = 2,   // spectrum -> b; r = d / max(b, eps)      -> spectrum of r
     XM_UPDATE = 3,  // spectrum -> q; u = u * q (stored)       -> spectrum of u
     XM_FINAL = 4,   // spectrum -> q; out = u * q
-    XM_COUNT = 5
+    XM_COUNT = 5,
+    // the adjoint passes of the differentiable path (one launch shape per length)
+    XM_ADJ_R = 5,   // spectrum -> rbar; dbar += rbar / c; bbar -> spectrum
+    XM_ADJ_U = 6    // [spectrum -> t]; g = w + t; qbar = g u -> spectrum, w = g q (or w = g)
 };
 
 struct XArgs {
@@ -76,6 +79,13 @@ struct XArgs {
     // linear-boundary plans (0: none): image row r = z * ny_img + y is spectrum row
     // z * ny_spec + y (the spectrum's planes have ny_spec >= ny_img rows)
     int64_t ny_img, ny_spec;
+    // the adjoint passes (XM_ADJ_*): adj_b the blur b and adj_dbar the image gradient
+    // (read-modify-write) of XM_ADJ_R; XM_ADJ_U: adj_w the running gradient of the iterate
+    // (read-modify-write), adj_u and adj_q the iterate u and the correlation q of the
+    // iteration whose qbar it transforms (null: it only stores g), spec_in null: no inverse
+    // transform (t = 0)
+    const float *adj_u, *adj_q, *adj_b;
+    float *adj_w, *adj_dbar;
 };
 
 struct YArgs {
@@ -298,8 +308,10 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     }
     __syncthreads();
     pdl_wait();  // the previous pass's output is complete from here on
+    // XM_ADJ_U without a spectrum (the first adjoint step of a segment) has no inverse part
+    const bool have_spec = MODE != XM_ADJ_U || a.spec_in != nullptr;
     if constexpr (kSpecIn) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && have_spec) {
             // the CTA's spectrum rows, one bulk copy each, into the line-pair regions
             const int64_t row0 = block * L * 2;
             const int64_t left = a.rows - row0;
@@ -353,28 +365,32 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             });
         }
     } else {
-        const bool landed = mbar_wait_bounded(&bar[1], 0, a.err, a.wait_ns);
-        if (!__syncthreads_and(landed)) return;
-        const float2 *q0 = lpair, *q1 = lpair + XB;
-        static_for<0, E>([&](auto i_) {
-            constexpr int i = CUBIC_CI(i_);
-            const int k = t + P * i;
-            const bool hi = 2 * k > N;
-            const int kk = hi ? N - k : k;
-            float2 A = ok0 ? q0[kk] : make_float2(0.f, 0.f);
-            float2 B = ok1 ? q1[kk] : make_float2(0.f, 0.f);
-            if (hi) {
-                A.y = -A.y;
-                B.y = -B.y;
-            }
-            if (k == 0 || 2 * k == N) {  // self-conjugate bins of a real line
-                A.y = 0.f;
-                B.y = 0.f;
-            }
-            v[i] = make_float2(A.x - B.y, A.y + B.x);  // A + i B
-        });
-        __syncthreads();  // the rows are read before the exchanges overwrite the region
-        FFT::inverse(v, sm, stw, t, sync);
+        if (!have_spec) {  // uniform over the launch
+            static_for<0, E>([&](auto i_) { v[CUBIC_CI(i_)] = make_float2(0.f, 0.f); });
+        } else {
+            const bool landed = mbar_wait_bounded(&bar[1], 0, a.err, a.wait_ns);
+            if (!__syncthreads_and(landed)) return;
+            const float2 *q0 = lpair, *q1 = lpair + XB;
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                const int k = t + P * i;
+                const bool hi = 2 * k > N;
+                const int kk = hi ? N - k : k;
+                float2 A = ok0 ? q0[kk] : make_float2(0.f, 0.f);
+                float2 B = ok1 ? q1[kk] : make_float2(0.f, 0.f);
+                if (hi) {
+                    A.y = -A.y;
+                    B.y = -B.y;
+                }
+                if (k == 0 || 2 * k == N) {  // self-conjugate bins of a real line
+                    A.y = 0.f;
+                    B.y = 0.f;
+                }
+                v[i] = make_float2(A.x - B.y, A.y + B.x);  // A + i B
+            });
+            __syncthreads();  // the rows are read before the exchanges overwrite the region
+            FFT::inverse(v, sm, stw, t, sync);
+        }
 
         // operand rows: shared memory (TMA) or global
         const float *p0, *p1;
@@ -398,6 +414,50 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
                 if (ok0) o0[n] = v[i].x;
                 if (ok1) o1[n] = v[i].y;
             });
+        } else if constexpr (MODE == XM_ADJ_R) {
+            // rbar = v: dbar += rbar / c and bbar = -rbar d / c^2 where b > eps (the clamp's
+            // derivative is 0 below it), c = max(b, eps); bbar is transformed
+            const float eps = a.eps;
+            const float *bb0 = a.adj_b + r0 * N, *bb1 = a.adj_b + r1 * N;
+            const float *d0 = a.d + r0 * N, *d1 = a.d + r1 * N;
+            float *e0 = a.adj_dbar + r0 * N, *e1 = a.adj_dbar + r1 * N;
+            static_for<0, E>([&](auto i_) {
+                constexpr int i = CUBIC_CI(i_);
+                const int n = t + P * i;
+                const float b0v = ok0 ? __ldg(bb0 + n) : 0.f, b1v = ok1 ? __ldg(bb1 + n) : 0.f;
+                const float c0 = fmaxf(b0v, eps), c1 = fmaxf(b1v, eps);
+                const float r0v = v[i].x, r1v = v[i].y;
+                if (ok0) e0[n] += r0v / c0;
+                if (ok1) e1[n] += r1v / c1;
+                v[i] = make_float2(b0v > eps ? -r0v * (ok0 ? __ldg(d0 + n) : 0.f) / (c0 * c0) : 0.f,
+                                   b1v > eps ? -r1v * (ok1 ? __ldg(d1 + n) : 0.f) / (c1 * c1) : 0.f);
+            });
+        } else if constexpr (MODE == XM_ADJ_U) {
+            // g = w + v, the gradient of the iterate (v = 0 without a spectrum); then either
+            // qbar = g u (transformed) and w = g q, the running gradient of the iteration
+            // before, or w = g.  One kernel serves every step of a segment, so that the
+            // arithmetic does not depend on where the checkpoints fall.
+            float *w0 = a.adj_w + r0 * N, *w1 = a.adj_w + r1 * N;
+            if (a.adj_u) {  // uniform over the launch
+                const float *u0 = a.adj_u + r0 * N, *u1 = a.adj_u + r1 * N;
+                const float *q0 = a.adj_q + r0 * N, *q1 = a.adj_q + r1 * N;
+                static_for<0, E>([&](auto i_) {
+                    constexpr int i = CUBIC_CI(i_);
+                    const int n = t + P * i;
+                    const float x0 = v[i].x + (ok0 ? w0[n] : 0.f), x1 = v[i].y + (ok1 ? w1[n] : 0.f);
+                    v[i] = make_float2(x0 * (ok0 ? __ldg(u0 + n) : 0.f), x1 * (ok1 ? __ldg(u1 + n) : 0.f));
+                    if (ok0) w0[n] = x0 * __ldg(q0 + n);
+                    if (ok1) w1[n] = x1 * __ldg(q1 + n);
+                });
+            } else {
+                static_for<0, E>([&](auto i_) {
+                    constexpr int i = CUBIC_CI(i_);
+                    const int n = t + P * i;
+                    if (ok0) w0[n] += v[i].x;
+                    if (ok1) w1[n] += v[i].y;
+                });
+                return;  // uniform over the launch: no forward transform
+            }
         } else if constexpr (MODE == XM_RATIO) {
             const float eps = a.eps;
             float *kb0 = a.keep_a + r0 * N, *kb1 = a.keep_a + r1 * N;
@@ -548,7 +608,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
         }
     }
 
-    if constexpr (MODE == XM_FWD || MODE == XM_RATIO || MODE == XM_UPDATE) {
+    if constexpr (MODE == XM_FWD || MODE == XM_RATIO || MODE == XM_UPDATE || MODE >= XM_ADJ_R) {
         // On lines longer than 1024 with more than 16 elements per thread, the passes that
         // run two transforms would keep every exchange address of the inverse transform
         // live across the pointwise step for reuse in the forward one (about 165 registers

@@ -56,6 +56,8 @@ struct AxisKernels {
     ZMultiLaunch zm = nullptr;
     int xm_lines = 0;  // line pairs per X CTA
     int m_cols = 16;   // columns per Y/Z CTA
+    // the adjoint X passes of the differentiable path (XM_ADJ_R, XM_ADJ_U), in one shape
+    XLaunch adj[2] = {};
 };
 
 // Table lookup; nullptr if n has no kernels.
@@ -422,6 +424,14 @@ AxisKernels make_axis()
     } else {
         k.xv[0] = make_xvariant<N, P0, S::lines(P0, 128)>();
         k.nx = 1;
+    }
+    {
+        // the split with at most 16 elements per thread where there is one: these passes
+        // carry more operands than the forward ones, and the wider split keeps registers low
+        constexpr int PA = (S::P1 > 0 && S::P1 * 16 <= 1024) ? S::P1 : P0;
+        constexpr int LA = S::lines(PA, 128);
+        k.adj[0] = launch_x<N, PA, LA, XM_ADJ_R>;
+        k.adj[1] = launch_x<N, PA, LA, XM_ADJ_U>;
     }
     // lines longer than 1024: a split with up to 40 elements per thread may need fewer
     // stages (2560: 40 x 8 x 8 instead of 20 x 4 x 4 x 4 x 2)
