@@ -424,10 +424,18 @@ def run_batched(cr, args, ranks=None):
             cr.cubic_rl_deconvolve(p, i, n_iter, eps, o)
 
     ms_p = timed(plain, reps)
+    # algorithmic bytes of one iteration of this rank's volumes (real H): the X ratio pass
+    # 16 S + 4 V, the update 16 S + 8 V, four Y passes 64 S, two Z passes 2 (16 + 4) S, with
+    # S = nz ny (nx / 2 + 1) spectrum elements and V voxels
+    it_bytes = sum(136 * s[0] * s[1] * (s[2] // 2 + 1) + 12 * s[0] * s[1] * s[2] for s in shapes)
+    peak, peak_src = hbm_peak()
+    value = vox * n_iter / (ms_b * 1e-3) / 1e9
     return {"workload": f"{len(all_shapes)} volumes, axes drawn from the 5-smooth lengths in [48,160], {n_iter} iterations",
-            "voxels": vox, "volumes_per_rank": [len(p) for p in cr.shard_volumes(all_shapes, world)], "value": round(vox * n_iter / (ms_b * 1e-3) / 1e9, 3), "unit": UNIT,
+            "voxels": vox, "volumes_per_rank": [len(p) for p in cr.shard_volumes(all_shapes, world)], "value": round(value, 3), "unit": UNIT,
             "ms": round(ms_b, 3), "graph_kernel_nodes": nodes, "plain_calls_ms": round(ms_p, 3),
-            "speedup_vs_plain_calls": round(ms_p / ms_b, 3)}
+            "speedup_vs_plain_calls": round(ms_p / ms_b, 3),
+            "model": {"bytes_per_voxel_iter": round(it_bytes / sum(int(np.prod(s)) for s in shapes), 2),
+                      "frac": round(it_bytes * n_iter / (ms_b * 1e-3) / 1e9 / peak, 4), "peak_source": peak_src}}
 
 
 def run_accel(cr, args, plan, d, n_iter: int, eps: float, plain_ms_per_iter: float):

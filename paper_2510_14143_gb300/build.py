@@ -2,14 +2,15 @@
 
 ``python -m paper_2510_14143_gb300.build`` (or ``build()``) compiles every
 ``csrc/*.cu`` for sm_103a with nvcc, in parallel, and links
-``_build/libcubic_rl.so``.  Objects are rebuilt only when a source or header
-is newer than them.
+``_build/libcubic_rl.so``.  An object is rebuilt only when its source, a local header
+that the source includes (directly or not) or this script is newer than it.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -31,15 +32,28 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _deps_mtime() -> float:
-    files = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
-    files.append(os.path.abspath(__file__))
-    return max(os.path.getmtime(f) for f in files)
+_INCLUDE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+
+
+def _deps_mtime(src: str) -> float:
+    """Newest modification time of src, the local headers it includes (transitively) and
+    this build script."""
+    seen, todo = set(), [os.path.abspath(src)]
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(f):
+            continue
+        seen.add(f)
+        with open(f, encoding="utf-8", errors="replace") as fh:
+            for inc in _INCLUDE.findall(fh.read()):
+                todo.append(os.path.normpath(os.path.join(os.path.dirname(f), inc)))
+    seen.add(os.path.abspath(__file__))
+    return max(os.path.getmtime(f) for f in seen)
 
 
 def _compile(nvcc: str, src: str, extra) -> str:
     obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
-    if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _deps_mtime()):
+    if os.path.exists(obj) and os.path.getmtime(obj) >= _deps_mtime(src):
         return obj
     tmp = obj + f".tmp{os.getpid()}"
     cmd = [nvcc, *NVCC_FLAGS, *extra, "-c", src, "-o", tmp]

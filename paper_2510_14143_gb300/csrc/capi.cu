@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../../include/cubic_rl.h"
+#include "lens.cuh"
 #include "registry.cuh"
 
 using namespace cubic;
@@ -2469,12 +2470,13 @@ extern "C" cubic_status_t cubic_fsc_split(cubic_rl_plan_t half_plan, const float
 
 // ------------------------------------------------------------------ batched deconvolution
 //
-// Many volumes of different sizes in one CUDA graph.  For every pass, the volumes
-// whose axis along that pass has the same length share one launch: the launch's
-// blocks are the concatenation of every member volume's blocks, and each block
-// finds its volume in a device-side table (k_*_multi).  The whole n_iter sequence
-// is captured once into a graph and replayed on later calls with the same
-// arguments.
+// Many volumes of different sizes in one CUDA graph.  For every pass, the volumes whose
+// axis along that pass has a length of one of the all-lengths classes (lens.cuh) share
+// one launch per class, whatever their lengths; the volumes of other lengths share one
+// launch per length (k_*pass with a MultiTable).  A launch's blocks are the
+// concatenation of every member volume's blocks, and each block finds its volume in a
+// device-side table.  The whole n_iter sequence is captured once into a graph and
+// replayed on later calls with the same arguments.
 
 namespace {
 
@@ -2499,6 +2501,14 @@ struct ZGroup {
     int shape;
 };
 
+// One all-lengths launch: the volumes of one length class
+template <class Args>
+struct LensGroup {
+    int cls;
+    LensTable<Args> *tab;
+    int64_t blocks;
+};
+
 struct BatchState {
     std::vector<cubic_rl_plan_s *> plans;
     std::vector<const float *> images;
@@ -2508,6 +2518,9 @@ struct BatchState {
     std::vector<XGroup> gx;
     std::vector<YGroup> gy;
     std::vector<ZGroup> gz;
+    std::vector<LensGroup<XArgs>> lx;
+    std::vector<LensGroup<YArgs>> ly;
+    std::vector<LensGroup<ZArgs>> lz;
     void *dmem = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -2534,14 +2547,20 @@ static cubic_status_t enqueue_batched(BatchState &b, cudaStream_t st)
     }
     if (b.n_iter == 0) return CUBIC_OK;
     auto xstage = [&](int mode) -> cubic_status_t {
+        for (const auto &g : b.lx) CUBIC_CUDA(launch_x_lens(g.cls, mode, g.tab, g.blocks, st));
         for (const XGroup &g : b.gx) CUBIC_CUDA(g.k->xv[g.shape].m[mode](g.tab, g.blocks, st));
         return CUBIC_OK;
     };
-    auto yzy = [&](int zmode) -> cubic_status_t {
-        for (const YGroup &g : b.gy) CUBIC_CUDA(g.k->yzv[g.shape].ym(g.tab, g.blocks, 0, st));
-        for (const ZGroup &g : b.gz) CUBIC_CUDA(g.k->yzv[g.shape].zm(g.tab, g.blocks, zmode, st));
-        for (const YGroup &g : b.gy) CUBIC_CUDA(g.k->yzv[g.shape].ym(g.tab, g.blocks, 1, st));
+    auto ystage = [&](int inverse) -> cubic_status_t {
+        for (const auto &g : b.ly) CUBIC_CUDA(launch_y_lens(g.cls, g.tab, g.blocks, inverse, st));
+        for (const YGroup &g : b.gy) CUBIC_CUDA(g.k->yzv[g.shape].ym(g.tab, g.blocks, inverse, st));
         return CUBIC_OK;
+    };
+    auto yzy = [&](int zmode) -> cubic_status_t {
+        if (cubic_status_t e = ystage(0)) return e;
+        for (const auto &g : b.lz) CUBIC_CUDA(launch_z_lens(g.cls, g.tab, g.blocks, zmode, st));
+        for (const ZGroup &g : b.gz) CUBIC_CUDA(g.k->yzv[g.shape].zm(g.tab, g.blocks, zmode, st));
+        return ystage(1);
     };
     cubic_status_t s = xstage(XM_FWD);
     for (int k = 0; k < b.n_iter && s == CUBIC_OK; ++k) {
@@ -2644,6 +2663,61 @@ static int64_t fill_ztable(const BatchState &b, const std::vector<int> &vols, co
 
 using LenGroups = std::map<int64_t, std::vector<int>>;
 
+// Host tables of the all-lengths launches of one class (volumes in order of length);
+// each returns the launch's block count.
+static int64_t fill_lens_x(const BatchState &b, const std::vector<int> &vols, LensTable<XArgs> *t)
+{
+    t->nvol = (int)vols.size();
+    int64_t blocks = 0;
+    for (int i = 0; i < t->nvol; ++i) {
+        cubic_rl_plan_s *p = b.plans[vols[i]];
+        XArgs a = x_args(p);
+        a.spec_in = p->ws;
+        a.spec_out = p->ws;
+        a.src = b.outs[vols[i]];
+        a.u = b.outs[vols[i]];
+        a.dst = b.outs[vols[i]];
+        a.d = b.images[vols[i]];
+        a.eps = b.eps;
+        t->args[i] = a;
+        t->len[i] = (int)p->nx;
+        t->prefix[i] = blocks;
+        blocks += lens_x_blocks((int)p->nx, p->rows);
+    }
+    t->prefix[t->nvol] = blocks;
+    return blocks;
+}
+
+static int64_t fill_lens_y(const BatchState &b, const std::vector<int> &vols, LensTable<YArgs> *t)
+{
+    t->nvol = (int)vols.size();
+    int64_t blocks = 0;
+    for (int i = 0; i < t->nvol; ++i) {
+        cubic_rl_plan_s *p = b.plans[vols[i]];
+        t->args[i] = y_args(p, p->ws, 0, 0, p->xh);
+        t->len[i] = (int)p->ny;
+        t->prefix[i] = blocks;
+        blocks += lens_col_blocks((int)p->ny, p->nz * p->xh);
+    }
+    t->prefix[t->nvol] = blocks;
+    return blocks;
+}
+
+static int64_t fill_lens_z(const BatchState &b, const std::vector<int> &vols, LensTable<ZArgs> *t)
+{
+    t->nvol = (int)vols.size();
+    int64_t blocks = 0;
+    for (int i = 0; i < t->nvol; ++i) {
+        cubic_rl_plan_s *p = b.plans[vols[i]];
+        t->args[i] = z_args(p, p->ws, ZM_CONV, 1.f, 0, p->xh);
+        t->len[i] = (int)p->nz;
+        t->prefix[i] = blocks;
+        blocks += lens_col_blocks((int)p->nz, p->ny * p->xh);
+    }
+    t->prefix[t->nvol] = blocks;
+    return blocks;
+}
+
 // Times every candidate shape of every group whose length has no chosen shape yet, on
 // the batch's own buffers, and records the fastest: X by a ratio and an update launch, Y
 // by a forward and an inverse, Z by one product.  The buffers are left with arbitrary
@@ -2740,16 +2814,33 @@ static cubic_status_t batch_tune(BatchState &b, const LenGroups &byx, const LenG
 static cubic_status_t build_batch(BatchState &b, cudaStream_t st)
 {
     const int n = (int)b.plans.size();
+    // all-lengths classes where the axis length has one (their line indices are 32-bit),
+    // else a launch per length
     LenGroups byx, byy, byz;
+    LenGroups lensx[kLensClasses], lensy[kLensClasses], lensz[kLensClasses];  // class -> length -> volumes
+    const int64_t kLines32 = (int64_t)1 << 31;
     for (int v = 0; v < n; ++v) {
-        byx[b.plans[v]->nx].push_back(v);
-        byy[b.plans[v]->ny].push_back(v);
-        byz[b.plans[v]->nz].push_back(v);
+        const cubic_rl_plan_s *p = b.plans[v];
+        const int cx = lens_class(p->nx), cy = lens_class(p->ny), cz = lens_class(p->nz);
+        if (cx >= 0) lensx[cx][p->nx].push_back(v);
+        else byx[p->nx].push_back(v);
+        if (cy >= 0 && p->nz * p->xh < kLines32) lensy[cy][p->ny].push_back(v);
+        else byy[p->ny].push_back(v);
+        if (cz >= 0 && p->ny * p->xh < kLines32) lensz[cz][p->nz].push_back(v);
+        else byz[p->nz].push_back(v);
     }
     cubic_status_t s = batch_tune(b, byx, byy, byz, st);
     if (s != CUBIC_OK) return s;
-    const size_t ntab = byx.size() + byy.size() + byz.size();
-    const size_t tsz = std::max({sizeof(MultiTable<XArgs>), sizeof(MultiTable<YArgs>), sizeof(MultiTable<ZArgs>)});
+    auto flat = [](const LenGroups &g) {
+        std::vector<int> vols;
+        for (auto &kv : g) vols.insert(vols.end(), kv.second.begin(), kv.second.end());
+        return vols;
+    };
+    size_t nlens = 0;
+    for (int c = 0; c < kLensClasses; ++c) nlens += !lensx[c].empty() + !lensy[c].empty() + !lensz[c].empty();
+    const size_t ntab = byx.size() + byy.size() + byz.size() + nlens;
+    const size_t tsz = std::max({sizeof(MultiTable<XArgs>), sizeof(MultiTable<YArgs>), sizeof(MultiTable<ZArgs>),
+                                 sizeof(LensTable<XArgs>), sizeof(LensTable<YArgs>), sizeof(LensTable<ZArgs>)});
     const size_t stride = (tsz + 255) / 256 * 256;
     std::vector<unsigned char> host(stride * ntab, 0);
     CUBIC_CUDA(cudaMalloc(&b.dmem, host.size()));
@@ -2779,6 +2870,30 @@ static cubic_status_t build_batch(BatchState &b, cudaStream_t st)
         b.gz.push_back({k, reinterpret_cast<MultiTable<ZArgs> *>(dbase + slot * stride), blocks, shape});
         ++slot;
     }
+    for (int c = 0; c < kLensClasses; ++c) {
+        if (!lensx[c].empty()) {
+            const int64_t blocks =
+                fill_lens_x(b, flat(lensx[c]), reinterpret_cast<LensTable<XArgs> *>(host.data() + slot * stride));
+            b.lx.push_back({c, reinterpret_cast<LensTable<XArgs> *>(dbase + slot * stride), blocks});
+            ++slot;
+        }
+        if (!lensy[c].empty()) {
+            const int64_t blocks =
+                fill_lens_y(b, flat(lensy[c]), reinterpret_cast<LensTable<YArgs> *>(host.data() + slot * stride));
+            b.ly.push_back({c, reinterpret_cast<LensTable<YArgs> *>(dbase + slot * stride), blocks});
+            ++slot;
+        }
+        if (!lensz[c].empty()) {
+            const int64_t blocks =
+                fill_lens_z(b, flat(lensz[c]), reinterpret_cast<LensTable<ZArgs> *>(host.data() + slot * stride));
+            b.lz.push_back({c, reinterpret_cast<LensTable<ZArgs> *>(dbase + slot * stride), blocks});
+            ++slot;
+        }
+    }
+    auto too_many = [](int64_t blocks) { return blocks > 0x7fffffff; };
+    for (const auto &g : b.lx) if (too_many(g.blocks)) return fail(CUBIC_ERR_INVALID_ARG, "batch too large for one launch");
+    for (const auto &g : b.ly) if (too_many(g.blocks)) return fail(CUBIC_ERR_INVALID_ARG, "batch too large for one launch");
+    for (const auto &g : b.lz) if (too_many(g.blocks)) return fail(CUBIC_ERR_INVALID_ARG, "batch too large for one launch");
     CUBIC_CUDA(cudaMemcpy(b.dmem, host.data(), host.size(), cudaMemcpyHostToDevice));
     return CUBIC_OK;
 }

@@ -1,0 +1,6 @@
+// All-lengths X pass of the batched path, mode XM_FINAL.
+#include "lens.cuh"
+
+namespace cubic {
+CUBIC_LENS_X_UNIT(XM_FINAL)
+}  // namespace cubic

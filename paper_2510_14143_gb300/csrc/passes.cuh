@@ -193,12 +193,14 @@ constexpr bool x_uses_tma()
 }
 
 // shared memory: [2 mbarriers | operand rows (TMA modes) | stage twiddles | line-pair regions]
-template <int N, int P, int L, int MODE, bool PF = false>
+// T: threads of the CTA.  Where T > P * L the threads past the L line pairs share one
+// spare line-pair region (they transform garbage there and touch no global memory).
+template <int N, int P, int L, int MODE, bool PF = false, int T = P * L>
 constexpr size_t x_smem_bytes()
 {
     return 16 + (x_uses_tma<N, MODE, PF>() ? (size_t)L * 2 * N * sizeof(float) : 0) +
            (size_t)((tw_table_size(N, N / P) + 1) / 2 * 2) * sizeof(float2) +
-           (size_t)L * x_smem_line<N, P>() * sizeof(float2);
+           (size_t)(L + (T > P * L ? 1 : 0)) * x_smem_line<N, P>() * sizeof(float2);
 }
 
 // Merges two compensated sums over the T threads of the CTA, in a fixed order
@@ -258,9 +260,12 @@ __device__ __forceinline__ void slot_add(float *pair, CFloat v)
     catomic_add(pair, pair + 1, -v.c);
 }
 
-template <int N, int P, int L, int MODE, bool PF>
+// T: threads of the CTA, P * L or more (the extra threads idle through the transforms on
+// a spare line-pair region, so that every thread meets every barrier)
+template <int N, int P, int L, int MODE, bool PF, int T = P * L>
 __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
 {
+    static_assert(T >= P * L && T < P * (L + 1), "a CTA of T threads holds L line pairs");
     constexpr int E = N / P;
     constexpr bool kTma = x_uses_tma<N, MODE, PF>();
     constexpr bool kPf = x_prefetches<N, MODE, PF>();
@@ -277,7 +282,8 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
     const int l = threadIdx.x / P;
     const int64_t m = block * L + l;
     const int64_t r0 = 2 * m, r1 = 2 * m + 1;
-    const bool ok0 = r0 < a.rows, ok1 = r1 < a.rows;
+    const bool live = T == P * L || l < L;
+    const bool ok0 = live && r0 < a.rows, ok1 = live && r1 < a.rows;
     // image row -> spectrum row (row indices stay below 2^32: nz, ny <= 65535)
     auto srow = [&](int64_t r) -> int64_t {
         if (a.ny_img <= 0) return r;
@@ -298,7 +304,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             bulk_prefetch_l2((MODE == XM_RATIO ? a.d : a.u) + row0 * N, (unsigned)(nrows * N * sizeof(float)));
         }
     }
-    FFT::fill_twiddles(stw, a.tw, threadIdx.x, P * L);  // plan constant: before the wait
+    FFT::fill_twiddles(stw, a.tw, threadIdx.x, T);  // plan constant: before the wait
     if constexpr (kTma || kSpecIn) {
         if (threadIdx.x == 0) {
             mbar_init(&bar[0], 1);
@@ -474,8 +480,8 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
                     if (ok0) c_nll = cf_add(c_nll, c0 - p0[n] * logf(c0));
                     if (ok1) c_nll = cf_add(c_nll, c1 - p1[n] * logf(c1));
                 });
-                const int slot = (int)((block * ((P * L + 31) / 32) + (threadIdx.x >> 5)) & 63);
-                slot_add<P * L>(a.nll_stats + 2 * slot, c_nll);
+                const int slot = (int)((block * ((T + 31) / 32) + (threadIdx.x >> 5)) & 63);
+                slot_add<T>(a.nll_stats + 2 * slot, c_nll);
             }
             if (kPf && !keep) {
                 // d from global memory: no store in this loop, so its loads issue together
@@ -583,9 +589,9 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             if (stats) {
                 // warp sums where the warp is full, else one add per thread
                 const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-                const int slot = (int)((block * ((P * L + 31) / 32) + warp) & 63);
+                const int slot = (int)((block * ((T + 31) / 32) + warp) & 63);
                 float *st4 = a.stats + 4 * slot;
-                if ((warp + 1) * 32 <= P * L) {
+                if ((warp + 1) * 32 <= T) {
                     for (int o = 16; o > 0; o >>= 1) {
                         s_num += __shfl_down_sync(0xffffffffu, s_num, o);
                         s_den += __shfl_down_sync(0xffffffffu, s_den, o);
@@ -601,7 +607,7 @@ __device__ __forceinline__ void x_body(const XArgs &a, const int64_t block)
             }
             if constexpr (MODE == XM_FINAL) {
                 if (acc) {  // uniform over the CTA
-                    const float4 tot = block_merge2<P * L>(c_num, c_den);
+                    const float4 tot = block_merge2<T>(c_num, c_den);
                     if (threadIdx.x == 0) a.acc_part[block] = tot;
                 }
             }

@@ -1,10 +1,13 @@
 """Batched deconvolution (many uneven volumes, one CUDA graph) against the plain path and the oracle.
 
-The batched path runs the same per-length transforms as the plain path, with the same
-threads per line (hence the same radix plan) but other kernels (tiles, loads): the
-results agree with the plain path to rounding (relative L2 <= 1e-6; the compiler may
-contract products into FMAs differently in different kernels), and with the FP64 oracle
-within the plain path's tolerance.
+Axis lengths of the all-lengths classes (48 to 160 here) run in one launch per class and
+pass, with their own threads per line (the fewest radix stages with at most 24 elements
+per thread, where a split allows it); other lengths run in one launch per length with the
+plain path's threads per line.  The radix plans then
+differ from the plain path's for some lengths, so the two agree to FP32 rounding of two
+different plans: each is within about 1e-6 (relative L2) of the FP64 oracle over these
+few iterations, so their difference is bounded here by 3e-6.  Against the oracle both
+keep the method's 1e-4.
 """
 import numpy as np
 import pytest
@@ -60,7 +63,52 @@ def test_batched_equals_plain_calls(cr):
         ref = torch.empty_like(img)
         cr.cubic_rl_deconvolve(plan, img, n_iter, 1e-6, ref)
         torch.cuda.synchronize()
-        assert rel_l2(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-6
+        assert rel_l2(out.cpu().numpy(), ref.cpu().numpy()) <= 3e-6
+
+
+def test_batched_one_launch_per_class_and_pass(cr):
+    # every axis length in a class: per iteration at most three launches (one per class) of
+    # each of the eight passes, beside each volume's three start-up kernels and the first
+    # forward transform; the per-length form needs one per distinct length
+    shapes = [(48, 50, 54), (60, 64, 72), (75, 80, 81), (81, 75, 90), (100, 96, 108), (50, 125, 48),
+              (135, 144, 150), (160, 128, 120)]
+    vols, plans, imgs = make_batch(cr, shapes, seed0=300)
+    outs = [torch.empty_like(i) for i in imgs]
+    n_iter = 5
+    cr.cubic_rl_deconvolve_batched(plans, imgs, n_iter, 1e-6, outs)
+    torch.cuda.synchronize()
+    assert cr.cubic_rl_batched_graph_nodes() <= 3 * len(shapes) + 3 + 24 * n_iter
+    for (d, psf), out in zip(vols, outs):
+        ref = oracle.rl(d, psf.cpu().numpy(), n_iter, 1e-6)
+        got = out.cpu().numpy().astype(np.float64)
+        assert rel_l2(got, ref) <= 1e-4
+        assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+def test_batched_asymmetric_psf(cr):
+    # a PSF without point symmetry: the Z pass multiplies by the complex H (convolution) and
+    # its conjugate (correlation) in the all-lengths kernels
+    shapes = [(48, 60, 64), (75, 54, 90)]
+    plans, imgs, vols = [], [], []
+    for j, shape in enumerate(shapes):
+        d, _ = synth.make_volume(shape, 20, (1.5, 3.0), 10.0, 1.5, 3.0, 7100 + j)
+        rng = np.random.Generator(np.random.PCG64(7200 + j))
+        g = np.meshgrid(*[np.arange(n) - n // 2 for n in shape], indexing="ij")
+        r2 = (g[0] / 2.0) ** 2 + (g[1] / 1.5) ** 2 + (g[2] / 1.2) ** 2
+        p = np.exp(-0.5 * r2) * (1.0 + 0.4 * (g[2] > 0) + 0.2 * (g[0] < 0)) + 1e-4 * rng.random(shape)
+        p = (p / p.sum()).astype(np.float32)
+        psf = torch.from_numpy(p).cuda()
+        plans.append(cr.cubic_rl_plan(shape, psf))
+        imgs.append(torch.from_numpy(d).cuda())
+        vols.append((d, p))
+    outs = [torch.empty_like(i) for i in imgs]
+    cr.cubic_rl_deconvolve_batched(plans, imgs, 9, 1e-6, outs)
+    torch.cuda.synchronize()
+    for (d, p), out in zip(vols, outs):
+        ref = oracle.rl(d, p, 9, 1e-6)
+        got = out.cpu().numpy().astype(np.float64)
+        assert rel_l2(got, ref) <= 1e-4
+        assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
 
 
 def test_batched_matches_oracle_and_replays(cr):
