@@ -540,7 +540,7 @@ def run_metrics(cr, args, plan, d, w: synth.Workload, plain_ms_per_iter: float):
                     "first_shell_below_1_7": int(below[0]) if below.size else None}}
 
 
-_paper_case = {}   # "case": (GPU estimate, image, PSF, iterations) of the paper-shaped volume
+_paper_case = {}   # "case": (image, launch shapes, iterations) of the paper-shaped volume
 
 
 def run_paper_shape(cr, args, keep_case: bool = False):
@@ -556,7 +556,6 @@ def run_paper_shape(cr, args, keep_case: bool = False):
     psf = torch.empty(shape, dtype=torch.float32, device="cuda")
     cr.cubic_psf_gaussian(shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0, psf)
     plan = cr.cubic_rl_plan(shape, psf)
-    psf_host = psf.cpu().numpy() if keep_case else None
     del psf
     out = torch.empty_like(d)
     cr.cubic_rl_autotune(plan, d, out)
@@ -585,11 +584,8 @@ def run_paper_shape(cr, args, keep_case: bool = False):
     flux = abs(out.double().sum().item() / d.double().sum().item() - 1.0)
     variants = list(cr.cubic_rl_plan_variants(plan)[1])
     if keep_case:
-        # for the accuracy leg: a short run of the timed plan, compared with the oracle later
-        n_acc = 2
-        cr.cubic_rl_deconvolve(plan, d, n_acc, eps, out)
-        torch.cuda.synchronize()
-        _paper_case["case"] = (out.cpu().numpy(), d.cpu().numpy(), psf_host, n_acc)
+        # for the accuracy leg: the image and the timed launch shapes
+        _paper_case["case"] = (d.cpu().numpy(), variants, 2)
     del plan
 
     # linear (zero-padded, same-mode) boundaries with a 31 x 33 x 33 PSF box, same data
@@ -768,11 +764,21 @@ def accuracy(cr, plan, d, d_host, w: synth.Workload, configs=None):
     timed volume (1024x1024x128) at its 50 in its benchmarked launch configuration.  Two stated
     subsets, where the oracle's Bluestein transforms of the non-power-of-two lengths are too
     slow for a bench run: the paper-shaped volume at 2 iterations, and 8 of the 64 batched
-    volumes (every eighth, from the fifth) at their 50.  Each entry gives rel_l2, max_rel, the
-    oracle's wall time on the host cores and, for the first two, the oracle's rate next to the
-    GPU's."""
+    volumes (every eighth, from the fifth) at their 50.  Both sides take the same PSF: the
+    oracle's Gaussian, rounded to float32 (the GPU's own PSF generator is checked against it
+    in the tests).  Each entry gives rel_l2, max_rel, the oracle's wall time on the host cores
+    and, for the first two, the oracle's rate next to the GPU's."""
     import torch
     import oracle
+
+    def host_psf(shape, sxy, sz):
+        return oracle.psf_gaussian(shape, sxy, sz, 1.0).astype(np.float32)
+
+    def plan_like(shape, psf32, variants=None):
+        p = cr.cubic_rl_plan(shape, torch.from_numpy(psf32).cuda())
+        if variants is not None:
+            cr.cubic_rl_plan_set_variants(p, *variants)
+        return p
 
     def run(plan_, img, n):
         out = torch.empty_like(img)
@@ -790,27 +796,33 @@ def accuracy(cr, plan, d, d_host, w: synth.Workload, configs=None):
 
     res = {}
     for wl in (synth.SMALL, synth.MEDIUM):
+        psf32 = host_psf(wl.shape, wl.psf_sigma_xy, wl.psf_sigma_z)
         if wl.name in _small_plans:
-            p, img, dh, psf = _small_plans[wl.name]
+            p0, img, dh, _ = _small_plans[wl.name]
+            p = plan_like(wl.shape, psf32, cr.cubic_rl_plan_variants(p0)[1])
         else:
             dh, _ = synth.workload_volume(wl)
             img = torch.from_numpy(dh).cuda()
-            psf = torch.empty(wl.shape, dtype=torch.float32, device="cuda")
-            cr.cubic_psf_gaussian(wl.shape, wl.psf_sigma_xy, wl.psf_sigma_z, 1.0, psf)
-            p = cr.cubic_rl_plan(wl.shape, psf)
-        r = with_oracle(run(p, img, wl.n_iter), dh, psf.cpu().numpy(), wl.n_iter)
+            p = plan_like(wl.shape, psf32)
+        r = with_oracle(run(p, img, wl.n_iter), dh, psf32, wl.n_iter)
         if configs and wl.name in configs:
             r["gpu_rate"] = configs[wl.name]["value"]
         res[wl.name] = r
-    psf = torch.empty(w.shape, dtype=torch.float32, device="cuda")
-    cr.cubic_psf_gaussian(w.shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0, psf)
-    res[w.name] = with_oracle(run(plan, d, w.n_iter), d_host, psf.cpu().numpy(), w.n_iter)
-    res[w.name]["launch_shapes_xyz"] = list(cr.cubic_rl_plan_variants(plan)[1])
-    del psf
+        del p
+    psf32 = host_psf(w.shape, w.psf_sigma_xy, w.psf_sigma_z)
+    shapes_xyz = list(cr.cubic_rl_plan_variants(plan)[1])
+    p = plan_like(w.shape, psf32, shapes_xyz)
+    res[w.name] = with_oracle(run(p, d, w.n_iter), d_host, psf32, w.n_iter)
+    res[w.name]["launch_shapes_xyz"] = shapes_xyz
+    del p
     if _paper_case:
-        got, dh, psf_h, n = _paper_case["case"]
-        res[synth.PAPER.name] = with_oracle(got, dh, psf_h, n)
-        res[synth.PAPER.name]["subset"] = f"{n} of {synth.PAPER.n_iter} iterations"
+        dh, variants, n = _paper_case["case"]
+        wp = synth.PAPER
+        psf32 = host_psf(wp.shape, wp.psf_sigma_xy, wp.psf_sigma_z)
+        p = plan_like(wp.shape, psf32, variants)
+        res[wp.name] = with_oracle(run(p, torch.from_numpy(dh).cuda(), n), dh, psf32, n)
+        res[wp.name]["subset"] = f"{n} of {wp.n_iter} iterations"
+        del p
     # batched workload: one batched call over the subset, each volume against the oracle
     all_shapes = synth.batch_shapes()
     picks = list(range(4, len(all_shapes), 8))
@@ -818,11 +830,10 @@ def accuracy(cr, plan, d, d_host, w: synth.Workload, configs=None):
     for j in picks:
         shape = all_shapes[j]
         dh, _ = synth.batch_volume(j, shape)
-        bpsf = torch.empty(shape, dtype=torch.float32, device="cuda")
-        cr.cubic_psf_gaussian(shape, synth.SMALL.psf_sigma_xy, synth.SMALL.psf_sigma_z, 1.0, bpsf)
-        plans.append(cr.cubic_rl_plan(shape, bpsf))
+        bpsf = host_psf(shape, synth.SMALL.psf_sigma_xy, synth.SMALL.psf_sigma_z)
+        plans.append(plan_like(shape, bpsf))
         imgs.append(torch.from_numpy(dh).cuda())
-        hosts.append((dh, bpsf.cpu().numpy()))
+        hosts.append((dh, bpsf))
     outs = [torch.empty_like(i) for i in imgs]
     cr.cubic_rl_deconvolve_batched(plans, imgs, synth.BATCH_ITERS, 1e-6, outs)
     torch.cuda.synchronize()
@@ -836,7 +847,8 @@ def accuracy(cr, plan, d, d_host, w: synth.Workload, configs=None):
     res["batched"] = {"n_iter": synth.BATCH_ITERS, "subset": f"volumes {picks} of {len(all_shapes)}",
                       "rel_l2": max(v["rel_l2"] for v in per), "max_rel": max(v["max_rel"] for v in per),
                       "oracle_s": round(t_or, 1), "per_volume": per}
-    res["reference"] = "FP64 CPU oracle, same inputs and PSF; rel_l2 and max_rel of the batched entry are the worst volume's"
+    res["reference"] = ("FP64 CPU oracle, same inputs and PSF (the oracle's Gaussian in float32); rel_l2 and "
+                        "max_rel of the batched entry are the worst volume's")
     return res
 
 

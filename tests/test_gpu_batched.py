@@ -33,14 +33,18 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def gaussian_psf(shape, sigma_xy, sigma_z):
+    # the oracle's Gaussian in float32: both sides take these values
+    return oracle.psf_gaussian(shape, sigma_xy, sigma_z, 1.0).astype(np.float32)
+
+
 def make_batch(cr, shapes, seed0=0):
     vols, plans, imgs = [], [], []
     for j, shape in enumerate(shapes):
         d, _ = synth.make_volume(shape, max(1, int(np.prod(shape)) // 20000), (1.5, 3.0), 10.0, 1.5, 3.0,
                                  5000 + seed0 + j)
-        psf = torch.empty(shape, dtype=torch.float32, device="cuda")
-        cr.cubic_psf_gaussian(shape, 1.5, 3.0, 1.0, psf)
-        plan = cr.cubic_rl_plan(shape, psf)
+        psf = gaussian_psf(shape, 1.5, 3.0)
+        plan = cr.cubic_rl_plan(shape, torch.from_numpy(psf).cuda())
         cr.cubic_rl_plan_set_variants(plan, 0, 0, 0)
         vols.append((d, psf))
         plans.append(plan)
@@ -79,7 +83,7 @@ def test_batched_one_launch_per_class_and_pass(cr):
     torch.cuda.synchronize()
     assert cr.cubic_rl_batched_graph_nodes() <= 3 * len(shapes) + 3 + 24 * n_iter
     for (d, psf), out in zip(vols, outs):
-        ref = oracle.rl(d, psf.cpu().numpy(), n_iter, 1e-6)
+        ref = oracle.rl(d, psf, n_iter, 1e-6)
         got = out.cpu().numpy().astype(np.float64)
         assert rel_l2(got, ref) <= 1e-4
         assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
@@ -120,7 +124,7 @@ def test_batched_matches_oracle_and_replays(cr):
     torch.cuda.synchronize()
     first = [o.clone() for o in outs]
     for (d, psf), out in zip(vols, outs):
-        ref = oracle.rl(d, psf.cpu().numpy(), n_iter, 1e-6)
+        ref = oracle.rl(d, psf, n_iter, 1e-6)
         assert rel_l2(out.cpu().numpy(), ref) <= 1e-4
     for o in outs:
         o.fill_(float("nan"))
@@ -140,11 +144,10 @@ def test_batched_workload_sample(cr):
     plans, imgs, vols = [], [], []
     for j, shape in zip(picks, shapes):
         d, _ = synth.batch_volume(j, shape)
-        psf = torch.empty(shape, dtype=torch.float32, device="cuda")
-        cr.cubic_psf_gaussian(shape, synth.SMALL.psf_sigma_xy, synth.SMALL.psf_sigma_z, 1.0, psf)
-        plans.append(cr.cubic_rl_plan(shape, psf))
+        psf = gaussian_psf(shape, synth.SMALL.psf_sigma_xy, synth.SMALL.psf_sigma_z)
+        plans.append(cr.cubic_rl_plan(shape, torch.from_numpy(psf).cuda()))
         imgs.append(torch.from_numpy(d).cuda())
-        vols.append((d, psf.cpu().numpy()))
+        vols.append((d, psf))
     outs = [torch.empty_like(i) for i in imgs]
     cr.cubic_rl_deconvolve_batched(plans, imgs, synth.BATCH_ITERS, 1e-6, outs)
     torch.cuda.synchronize()

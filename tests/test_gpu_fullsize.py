@@ -30,9 +30,9 @@ def cr():
 def large(cr):
     w = synth.LARGE
     d, _ = synth.workload_volume(w)
-    psf = torch.empty(w.shape, dtype=torch.float32, device="cuda")
-    cr.cubic_psf_gaussian(w.shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0, psf)
-    plan = cr.cubic_rl_plan(w.shape, psf)
+    # the oracle's Gaussian in float32: both sides take these values
+    psf = oracle.psf_gaussian(w.shape, w.psf_sigma_xy, w.psf_sigma_z, 1.0).astype(np.float32)
+    plan = cr.cubic_rl_plan(w.shape, torch.from_numpy(psf).cuda())
     dd = torch.from_numpy(d).cuda()
     out = torch.empty_like(dd)
     cr.cubic_rl_autotune(plan, dd, out)
@@ -48,7 +48,7 @@ def test_large_two_iterations_match_oracle(cr, large):
     out = torch.empty_like(dd)
     cr.cubic_rl_deconvolve(plan, dd, 2, 1e-6, out)
     torch.cuda.synchronize()
-    ref = oracle.rl(d, psf.cpu().numpy(), 2, 1e-6)
+    ref = oracle.rl(d, psf, 2, 1e-6)
     got = out.cpu().numpy().astype(np.float64)
     err = rel_l2(got, ref)
     worst = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
