@@ -706,14 +706,19 @@ def load_traffic(kinds, w: synth.Workload):
 
 
 def source_hash() -> str:
-    """Hash of the files the pass kernels compile from (csrc/*.cuh and the shard units;
-    capi.cu, the host side and the small reduction kernels, is left out)."""
+    """Hash of the files the plain path's pass kernels compile from: the shard units and the
+    headers they include (capi.cu, the host side and the small reduction kernels, and the
+    batched path's all-lengths kernels are left out)."""
+    import glob
     import hashlib
-    h = hashlib.sha256()
+    from paper_2510_14143_gb300 import build as _build
     csrc = os.path.join(ROOT, "paper_2510_14143_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")) and fn != "capi.cu":
-            h.update(open(os.path.join(csrc, fn), "rb").read())
+    files = set()
+    for src in glob.glob(os.path.join(csrc, "shard_*.cu")):
+        files |= _build.source_files(src)
+    h = hashlib.sha256()
+    for f in sorted(files, key=os.path.basename):
+        h.update(open(f, "rb").read())
     return h.hexdigest()[:12]
 
 

@@ -35,9 +35,8 @@ def _nvcc() -> str:
 _INCLUDE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
 
 
-def _deps_mtime(src: str) -> float:
-    """Newest modification time of src, the local headers it includes (transitively) and
-    this build script."""
+def source_files(src: str) -> set:
+    """src and the local headers it includes, directly or not."""
     seen, todo = set(), [os.path.abspath(src)]
     while todo:
         f = todo.pop()
@@ -47,8 +46,12 @@ def _deps_mtime(src: str) -> float:
         with open(f, encoding="utf-8", errors="replace") as fh:
             for inc in _INCLUDE.findall(fh.read()):
                 todo.append(os.path.normpath(os.path.join(os.path.dirname(f), inc)))
-    seen.add(os.path.abspath(__file__))
-    return max(os.path.getmtime(f) for f in seen)
+    return seen
+
+
+def _deps_mtime(src: str) -> float:
+    """Newest modification time of src, the local headers it includes and this build script."""
+    return max(os.path.getmtime(f) for f in source_files(src) | {os.path.abspath(__file__)})
 
 
 def _compile(nvcc: str, src: str, extra) -> str:

@@ -183,11 +183,23 @@ __global__ void __launch_bounds__(kReduceThreads) k_sum_final(const double *__re
     }
 }
 
+// max(sum / V, eps), once per CTA: the double division is slow on this GPU's FP64 units,
+// and small volumes launch one thread per voxel
+__device__ __forceinline__ float initial_value_block(const double *__restrict__ sum, int64_t V, float eps)
+{
+    __shared__ float v_sh;
+    if (threadIdx.x == 0) {
+        const double m = sum[0] / (double)V;
+        v_sh = m > (double)eps ? (float)m : eps;
+    }
+    __syncthreads();
+    return v_sh;
+}
+
 // u0 = max(sum / V, eps) everywhere.
 __global__ void k_fill_initial(float *__restrict__ u, int64_t V, const double *__restrict__ sum, float eps)
 {
-    const double m = sum[0] / (double)V;
-    const float v = m > (double)eps ? (float)m : eps;
+    const float v = initial_value_block(sum, V, eps);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x)
         u[i] = v;
 }
@@ -842,8 +854,7 @@ __global__ void k_crop_rows(const float *__restrict__ in, float *__restrict__ ou
 __global__ void k_fill_padded(float *__restrict__ u, int64_t rows, int64_t nvalid, int64_t n,
                               const double *__restrict__ sum, int64_t V, float eps)
 {
-    const double m = sum[0] / (double)V;
-    const float v = m > (double)eps ? (float)m : eps;
+    const float v = initial_value_block(sum, V, eps);
     const int64_t total = rows * n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
         u[i] = (i % n) < nvalid ? v : 0.f;

@@ -80,15 +80,15 @@ constexpr int lens_class(int64_t n)
 }
 
 // CTAs per SM a kernel is compiled for, which sets its register budget per thread.  The
-// light class: the largest count at which its heaviest body (X: the update) does not
-// spill.  The others: 128 registers, at which the bodies of 24 and 30 elements per thread
-// spill a little (up to 160 bytes a thread), for a third more warps per SM than at 168.
+// light class: 102 registers, at which none of its bodies spills.  The others: 128, at
+// which the bodies of 24 and 30 elements per thread spill a little (up to 160 bytes a
+// thread), for a third more warps per SM than at 168.
 enum LensKind : int { LK_X = 0, LK_Y = 1, LK_Z = 2 };
 template <class Lens, int KIND>
 constexpr int lens_min_blocks()
 {
     if constexpr (Lens::max_elems() <= 16)
-        return KIND == LK_X ? 4 : 5;  // 128 or 102 registers
+        return 5;  // 102 registers
     else
         return 4;                     // 128
 }
