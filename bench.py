@@ -903,6 +903,25 @@ def run_ncu_target(args, w: synth.Workload):
     torch.cuda.synchronize()
 
 
+def run_ncu_batched(args):
+    """Profiling target: the batched leg's 64 plans, then three batched calls of
+    --ncu-iters iterations (the first captures the graph); no timing, no line."""
+    import torch
+    import paper_2510_14143_gb300 as cr
+    shapes = synth.batch_shapes()
+    plans, imgs, outs = [], [], []
+    for j, shape in enumerate(shapes):
+        d, _ = synth.batch_volume(j, shape)
+        psf = torch.empty(shape, dtype=torch.float32, device="cuda")
+        cr.cubic_psf_gaussian(shape, synth.SMALL.psf_sigma_xy, synth.SMALL.psf_sigma_z, 1.0, psf)
+        plans.append(cr.cubic_rl_plan(shape, psf))
+        imgs.append(torch.from_numpy(d).cuda())
+        outs.append(torch.empty(shape, dtype=torch.float32, device="cuda"))
+    for _ in range(3):
+        cr.cubic_rl_deconvolve_batched(plans, imgs, args.ncu_iters, 1e-6, outs)
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -922,6 +941,8 @@ def main():
                     help="skip the comparison with the FP64 oracle at the stated iteration counts (minutes of CPU)")
     ap.add_argument("--ncu-target", metavar="VX,VY,VZ",
                     help="profiling target only: plan + --ncu-iters RL iterations with these launch shapes")
+    ap.add_argument("--ncu-batched", action="store_true",
+                    help="profiling target only: the 64-volume batched workload, three calls of --ncu-iters iterations")
     ap.add_argument("--ncu-iters", type=int, default=1)
     ap.add_argument("--variants", metavar="VX,VY,VZ",
                     help="pin the launch shapes of the timed workload instead of autotuning")
@@ -929,6 +950,9 @@ def main():
     w = synth.PLAIN[args.workload]
     if args.ncu_target:
         run_ncu_target(args, w)
+        return
+    if args.ncu_batched:
+        run_ncu_batched(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
