@@ -112,10 +112,12 @@ CUBIC_API cubic_status_t cubic_rl_deconvolve(cubic_rl_plan_t plan, const float *
 /* Batched Richardson-Lucy: the same deconvolution as cubic_rl_deconvolve for n volumes of
  * possibly different sizes, each with its own plan (plans must be distinct: a plan's scratch
  * serves one volume).  images[v], outs[v]: device float32 volumes of plans[v]'s dims.  For
- * each pass, all volumes with the same length along that pass share one kernel launch whose
- * blocks span every member volume.  The launch shape of each such launch (threads per line,
- * lines or columns per CTA) is tuned the first time a length appears: every candidate is
- * timed on the call's own buffers and the fastest is kept for the process.  The whole
+ * each pass, the volumes whose length along that pass is one of the 5-smooth lengths 48 to
+ * 160 share one kernel launch per length class (three classes by elements per thread, with
+ * launch shapes fixed per length); the volumes of any other length share one launch per
+ * length, whose launch shape (threads per line, lines or columns per CTA) is tuned the first
+ * time the length appears: every candidate is timed on the call's own buffers and the
+ * fastest is kept for the process.  A launch's blocks span every member volume.  The whole
  * n_iter sequence is captured once into a CUDA graph (first call with a given argument
  * set: tuning of new lengths, capture and instantiation, synchronous) and replayed on
  * `stream` by later calls with identical arguments (a few argument sets are cached).
