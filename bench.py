@@ -18,7 +18,7 @@ Multi-GPU: a single volume does not shard, so ranks run independent replicas
 (weak scaling); the only collectives are the host-side barrier and the max of
 the elapsed time.
 
---impl reference times the FP64 CPU oracle (the reference for this build) on a
+--impl reference times the FP64 CPU oracle (the reference arm) on a
 bounded sample of the same workload on the host cores.
 """
 from __future__ import annotations
